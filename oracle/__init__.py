@@ -1,0 +1,229 @@
+"""Plain FP64 CPU oracle for the symmetric eigenvalue path (arXiv 1604.03703).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` leg of ``bench.py`` may import this
+package; the product path (``paper_1604_03703_gb300``) never does.  The
+arithmetic lives in ``oracle.c`` (plain C, FP64, no fused multiply-add); this
+module only builds it and marshals numpy arrays.  See ``oracle.c`` for the
+paper passage each function follows.
+
+Parity status: every function here is pinned by tests in
+``tests/test_oracle_pins.py`` against closed forms, brute-force Jacobi,
+LDL^T inertia counts, invariants of orthogonal similarity and the band
+structure the paper's algorithms ensure.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = ctypes.POINTER(ctypes.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2, no FP contraction)."""
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            i, d = ctypes.c_int, ctypes.c_double
+            lib.orc_house.restype = d
+            lib.orc_house.argtypes = [i, _dp, i, _dp]
+            lib.orc_tridiagonalize.restype = None
+            lib.orc_tridiagonalize.argtypes = [i, _dp, i, _dp, _dp, i]
+            lib.orc_pivmin.restype = d
+            lib.orc_pivmin.argtypes = [i, _dp]
+            lib.orc_sturm_count.restype = i
+            lib.orc_sturm_count.argtypes = [i, _dp, _dp, d, d]
+            lib.orc_gershgorin.restype = d
+            lib.orc_gershgorin.argtypes = [i, _dp, _dp, d, _dp, _dp]
+            lib.orc_bisect.restype = i
+            lib.orc_bisect.argtypes = [i, _dp, _dp, d, i, _dp]
+            lib.orc_eigvalsh.restype = i
+            lib.orc_eigvalsh.argtypes = [i, _dp, i, d, _dp]
+            lib.orc_jacobi.restype = i
+            lib.orc_jacobi.argtypes = [i, _dp, i, _dp]
+            lib.orc_inertia.restype = i
+            lib.orc_inertia.argtypes = [i, _dp, i, d]
+            lib.orc_panel_qr.restype = i
+            lib.orc_panel_qr.argtypes = [i, i, _dp, i, _dp, i, _dp, i]
+            lib.orc_full_to_band.restype = None
+            lib.orc_full_to_band.argtypes = [i, _dp, i, i]
+            lib.orc_band_to_band.restype = None
+            lib.orc_band_to_band.argtypes = [i, _dp, i, i, i, i, ctypes.c_long]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _fortran(a) -> np.ndarray:
+    """Column-major FP64 copy (the oracle's storage order)."""
+    return np.array(a, dtype=np.float64, order="F", copy=True)
+
+
+# ---------------------------------------------------------------- reflectors
+def house(x):
+    """Householder reflector of x: returns (v, tau, beta) with v[0] = 1 and
+    (I - tau v v^T) x = beta e_1; "always reflect" sign rule (Lemma 3.4)."""
+    x = np.array(x, dtype=np.float64, copy=True)
+    beta = ctypes.c_double()
+    tau = _load().orc_house(x.size, _ptr(x), 1, ctypes.byref(beta))
+    v = x.copy()
+    v[0] = 1.0
+    return v, tau, beta.value
+
+
+# ------------------------------------------------------- tridiagonal / Sturm
+def tridiagonalize(A, nsteps: int = -1):
+    """Unblocked Householder tridiagonalisation (Algorithm 4.1 with b = 1).
+    Reads the lower triangle of A; returns (d, e)."""
+    M = _fortran(A)
+    n = M.shape[0]
+    d = np.zeros(max(n, 1))
+    e = np.zeros(max(n, 1))
+    _load().orc_tridiagonalize(n, _ptr(M), n, _ptr(d), _ptr(e), nsteps)
+    return d[:n], e[: max(n - 1, 0)]
+
+
+def tridiagonalize_inplace(M: np.ndarray, d: np.ndarray, e: np.ndarray, nsteps: int) -> None:
+    """In-place form used to time a bounded sample of the reduction."""
+    assert M.flags.f_contiguous and M.dtype == np.float64
+    _load().orc_tridiagonalize(M.shape[0], _ptr(M), M.shape[0], _ptr(d), _ptr(e), nsteps)
+
+
+def pivmin(e) -> float:
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    return _load().orc_pivmin(e.size + 1, _ptr(e) if e.size else _ptr(np.zeros(1)))
+
+
+def sturm_count(d, e, x: float) -> int:
+    """Number of eigenvalues of T(d, e) below x (negative LDL^T pivots)."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    e = np.ascontiguousarray(e, dtype=np.float64)
+    n = d.size
+    e2 = np.zeros(max(n, 1))
+    e2[: n - 1] = e * e
+    pm = pivmin(e)
+    return _load().orc_sturm_count(n, _ptr(d), _ptr(e2), float(x), pm)
+
+
+def gershgorin(d, e):
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    e = np.ascontiguousarray(np.append(e, 0.0), dtype=np.float64)
+    gl, gu = ctypes.c_double(), ctypes.c_double()
+    tn = _load().orc_gershgorin(d.size, _ptr(d), _ptr(e), pivmin(e[:-1]), ctypes.byref(gl), ctypes.byref(gu))
+    return gl.value, gu.value, tn
+
+
+def bisect(d, e, rtol: float = 1e-14, maxit: int = 200, return_noconv: bool = False):
+    """All eigenvalues of the tridiagonal T(d, e), ascending, by bisection."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = d.size
+    ee = np.zeros(max(n, 1))
+    ee[: n - 1] = np.asarray(e, dtype=np.float64)[: n - 1]
+    out = np.zeros(max(n, 1))
+    nc = _load().orc_bisect(n, _ptr(d), _ptr(ee), float(rtol), int(maxit), _ptr(out))
+    return (out[:n], nc) if return_noconv else out[:n]
+
+
+def eigvalsh(A, rtol: float = 1e-14):
+    """Eigenvalues of symmetric A (lower triangle read), ascending."""
+    M = _fortran(A)
+    n = M.shape[0]
+    out = np.zeros(max(n, 1))
+    _load().orc_eigvalsh(n, _ptr(M), n, float(rtol), _ptr(out))
+    return out[:n]
+
+
+# ------------------------------------------------------------- cross-checks
+def jacobi(A):
+    """Cyclic Jacobi eigenvalues (ascending), lower triangle read."""
+    M = _fortran(A)
+    n = M.shape[0]
+    out = np.zeros(max(n, 1))
+    _load().orc_jacobi(n, _ptr(M), n, _ptr(out))
+    return out[:n]
+
+
+def inertia(A, x: float) -> int:
+    """Number of eigenvalues of A below x via long-double LDL^T of A - xI."""
+    M = _fortran(A)
+    return _load().orc_inertia(M.shape[0], _ptr(M), M.shape[0], float(x))
+
+
+# ------------------------------------------------------------- stage oracles
+def panel_qr(P):
+    """Householder QR of the m x nc panel: returns (R, U, T, r) with
+    P = (I - U T U^T)[:, :] @ [R; 0] and r = min(nc, m-1) reflectors."""
+    P = _fortran(P)
+    m, nc = P.shape
+    r_max = max(min(nc, m - 1), 1)
+    U = np.zeros((m, r_max), order="F")
+    T = np.zeros((r_max, r_max), order="F")
+    r = _load().orc_panel_qr(m, nc, _ptr(P), m, _ptr(U), m, _ptr(T), r_max)
+    return P, U[:, :r], T[:r, :r], r
+
+
+def full_to_band(A, b: int):
+    """Algorithm 4.1 (right-looking): returns the full symmetric band matrix."""
+    M = _fortran(A)
+    M = np.tril(M) + np.tril(M, -1).T  # full symmetric storage from the lower triangle
+    M = np.asfortranarray(M)
+    _load().orc_full_to_band(M.shape[0], _ptr(M), M.shape[0], int(b))
+    return M
+
+
+def band_to_band(B, b: int, h: int, nc_paper: bool = False, max_chases: int = -1):
+    """Algorithm 4.2 (b -> h) on dense storage: returns the full symmetric
+    result (after ``max_chases`` chases when that is >= 0)."""
+    M = _fortran(B)
+    M = np.tril(M) + np.tril(M, -1).T
+    M = np.asfortranarray(M)
+    _load().orc_band_to_band(M.shape[0], _ptr(M), M.shape[0], int(b), int(h), 1 if nc_paper else 0, int(max_chases))
+    return M
+
+
+def band_schedule(b0: int):
+    """Halving schedule b0 -> b0/2 -> ... -> 1 (Algorithm 4.3 with k = 2);
+    an odd b stops the halving with one final b -> 1 step."""
+    s = [b0]
+    while s[-1] > 1:
+        b = s[-1]
+        s.append(b // 2 if b % 2 == 0 else 1)
+    return s
+
+
+def eigvalsh_via_stages(A, b0: int, rtol: float = 1e-14):
+    """Algorithm 4.3 on one processor: full-to-band, band halvings, bisection."""
+    M = full_to_band(A, b0)
+    sched = band_schedule(b0)
+    for b, h in zip(sched[:-1], sched[1:]):
+        M = band_to_band(M, b, h)
+    d = np.diag(M).copy()
+    e = np.diag(M, -1).copy()
+    return bisect(d, e, rtol)
