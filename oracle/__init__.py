@@ -73,6 +73,8 @@ def _load():
             lib.orc_full_to_band.argtypes = [i, _dp, i, i]
             lib.orc_band_to_band.restype = None
             lib.orc_band_to_band.argtypes = [i, _dp, i, i, i, i, ctypes.c_long]
+            lib.orc_band_to_band_wavefront.restype = None
+            lib.orc_band_to_band_wavefront.argtypes = [i, _dp, i, i, i, i, i]
             _lib = lib
     return _lib
 
@@ -205,6 +207,17 @@ def band_to_band(B, b: int, h: int, nc_paper: bool = False, max_chases: int = -1
     M = np.tril(M) + np.tril(M, -1).T
     M = np.asfortranarray(M)
     _load().orc_band_to_band(M.shape[0], _ptr(M), M.shape[0], int(b), int(h), 1 if nc_paper else 0, int(max_chases))
+    return M
+
+
+def band_to_band_wavefront(B, b: int, h: int, wave: int, tie_desc: bool = False):
+    """Algorithm 4.2's chases run in wavefront order t = wave*i + j (ties in
+    increasing or decreasing i); equals band_to_band bit for bit iff the
+    pipelined schedule is legal."""
+    M = _fortran(B)
+    M = np.tril(M) + np.tril(M, -1).T
+    M = np.asfortranarray(M)
+    _load().orc_band_to_band_wavefront(M.shape[0], _ptr(M), M.shape[0], int(b), int(h), int(wave), 1 if tie_desc else 0)
     return M
 
 

@@ -498,9 +498,9 @@ void orc_full_to_band(int n, double *A, int lda, int b)
 }
 
 /*
- * Algorithm 4.2 (band-to-band, b -> h with h | b) on dense full symmetric
- * storage, sweeps i and chases j in the sequential order the algorithm
- * writes.  Offsets (1-based i, j as in the algorithm; 0-based storage):
+ * One chase (i, j) of Algorithm 4.2 (band-to-band, b -> h with h | b) on
+ * dense full symmetric storage.  Offsets (1-based i, j as in the algorithm;
+ * 0-based storage):
  *   o_blg = (i-1)h + (j-1)b,  o_qr.r = o_blg + h
  *   j = 1: o_qr.c = o_qr.r - h, o_v = 0, o_up.c = o_qr.r     (reading A5)
  *   j > 1: o_qr.c = o_qr.r - b, o_v = b - h, o_up.c = o_qr.c + h
@@ -509,108 +509,98 @@ void orc_full_to_band(int n, double *A, int lda, int b)
  *         (reading A6; nc_paper != 0 uses the printed min(n - o_up.c, h + 3b)
  *         instead, which must give the same result because the extra rows
  *         are exactly zero)
- *   sweeps i while n - ih >= 2; chases j while n - o_qr.r >= 2   (reading A7)
  *   QR of the n_r x h block B[I_qr.rs, I_qr.cs] (reading A8)
- * Each chase: [U,T,R] = QR(B[qr rows, qr cols]); write [R;0] and its
- * transpose; W = B[up cols, qr rows] U T; V = -W;
+ * Steps: [U,T,R] = QR(B[qr rows, qr cols]); write [R;0] and its transpose;
+ * W = B[up cols, qr rows] U T; V = -W;
  * V[v rows] += (1/2) U (T^T (U^T W[v rows])); B[qr rows, up cols] += U V^T;
  * B[up cols, qr rows] += V U^T.
- * max_chases >= 0 stops after that many chases (to inspect intermediate
- * fill); max_chases < 0 runs the whole reduction.
+ * Returns 0 if the chase does not exist (n - o_qr.r < 2, reading A7).
  */
-void orc_band_to_band(int n, double *B, int ldb, int b, int h, int nc_paper, long max_chases)
+static int orc_chase(int n, double *B, int ldb, int b, int h, int i, int j, int nc_paper)
 {
-    long done = 0;
-    if (h < 1 || b <= h || b % h != 0) return;
+    int o_blg = (i - 1) * h + (j - 1) * b;
+    int o_qr_r = o_blg + h;
+    if (n - o_qr_r < 2) return 0;
+    int o_qr_c, o_v, o_up_c, n_c;
+    if (j == 1) {
+        o_qr_c = o_qr_r - h;
+        o_v = 0;
+        o_up_c = o_qr_r;
+    } else {
+        o_qr_c = o_qr_r - b;
+        o_v = b - h;
+        o_up_c = o_qr_c + h;
+    }
+    int n_r = n - o_qr_r < b ? n - o_qr_r : b;
+    int lim = nc_paper ? (h + 3 * b) : (j == 1 ? 2 * b : 3 * b - h);
+    n_c = n - o_up_c < lim ? n - o_up_c : lim;
+    int ncmax = 3 * b + h + 1;
     double *Q = (double *)malloc(sizeof(double) * (size_t)b * (size_t)h);
     double *U = (double *)malloc(sizeof(double) * (size_t)b * (size_t)h);
     double *T = (double *)malloc(sizeof(double) * (size_t)h * (size_t)h);
-    int ncmax = 3 * b + h + 1;
     double *W = (double *)malloc(sizeof(double) * (size_t)ncmax * (size_t)h);
     double *V = (double *)malloc(sizeof(double) * (size_t)ncmax * (size_t)h);
     double *S = (double *)malloc(sizeof(double) * (size_t)h * (size_t)h);
     double *Z = (double *)malloc(sizeof(double) * (size_t)h * (size_t)h);
-    for (int i = 1; n - i * h >= 2; ++i) {
-        for (int j = 1;; ++j) {
-            int o_blg = (i - 1) * h + (j - 1) * b;
-            int o_qr_r = o_blg + h;
-            if (n - o_qr_r < 2) break;
-            if (max_chases >= 0 && done >= max_chases) goto finished;
-            ++done;
-            int o_qr_c, o_v, o_up_c, n_c;
-            if (j == 1) {
-                o_qr_c = o_qr_r - h;
-                o_v = 0;
-                o_up_c = o_qr_r;
-            } else {
-                o_qr_c = o_qr_r - b;
-                o_v = b - h;
-                o_up_c = o_qr_c + h;
-            }
-            int n_r = n - o_qr_r < b ? n - o_qr_r : b;
-            int lim = nc_paper ? (h + 3 * b) : (j == 1 ? 2 * b : 3 * b - h);
-            n_c = n - o_up_c < lim ? n - o_up_c : lim;
-            /* QR of the n_r x h block */
-            for (int c = 0; c < h; ++c)
-                for (int r = 0; r < n_r; ++r) Q[IDX(r, c, n_r)] = B[IDX(o_qr_r + r, o_qr_c + c, ldb)];
-            int nr = orc_panel_qr(n_r, h, Q, n_r, U, n_r, T, h);
-            for (int c = 0; c < h; ++c)
-                for (int r = 0; r < n_r; ++r) {
-                    B[IDX(o_qr_r + r, o_qr_c + c, ldb)] = Q[IDX(r, c, n_r)];
-                    B[IDX(o_qr_c + c, o_qr_r + r, ldb)] = Q[IDX(r, c, n_r)];
-                }
-            if (nr == 0) continue;
-            /* W = B[up cols, qr rows] U T */
-            for (int c = 0; c < nr; ++c)
-                for (int r = 0; r < n_c; ++r) {
-                    double s = 0.0;
-                    for (int q = 0; q < n_r; ++q) s += B[IDX(o_up_c + r, o_qr_r + q, ldb)] * U[IDX(q, c, n_r)];
-                    V[IDX(r, c, n_c)] = s; /* V used as scratch for B U */
-                }
-            for (int c = 0; c < nr; ++c)
-                for (int r = 0; r < n_c; ++r) {
-                    double s = 0.0;
-                    for (int q = 0; q <= c; ++q) s += V[IDX(r, q, n_c)] * T[IDX(q, c, h)];
-                    W[IDX(r, c, n_c)] = s;
-                }
-            /* V = -W */
-            for (int c = 0; c < nr; ++c)
-                for (int r = 0; r < n_c; ++r) V[IDX(r, c, n_c)] = -W[IDX(r, c, n_c)];
-            /* S = U^T W[v rows], Z = T^T S, V[v rows] += 0.5 U Z */
-            for (int c = 0; c < nr; ++c)
-                for (int a = 0; a < nr; ++a) {
-                    double s = 0.0;
-                    for (int q = 0; q < n_r; ++q) s += U[IDX(q, a, n_r)] * W[IDX(o_v + q, c, n_c)];
-                    S[IDX(a, c, h)] = s;
-                }
-            for (int c = 0; c < nr; ++c)
-                for (int a = 0; a < nr; ++a) {
-                    double s = 0.0;
-                    for (int q = 0; q <= a; ++q) s += T[IDX(q, a, h)] * S[IDX(q, c, h)];
-                    Z[IDX(a, c, h)] = s;
-                }
-            for (int c = 0; c < nr; ++c)
-                for (int q = 0; q < n_r; ++q) {
-                    double s = 0.0;
-                    for (int a = 0; a < nr; ++a) s += U[IDX(q, a, n_r)] * Z[IDX(a, c, h)];
-                    V[IDX(o_v + q, c, n_c)] += 0.5 * s;
-                }
-            /* B[qr rows, up cols] += U V^T ; B[up cols, qr rows] += V U^T */
-            for (int cc = 0; cc < n_c; ++cc)
-                for (int q = 0; q < n_r; ++q) {
-                    double s = 0.0;
-                    for (int a = 0; a < nr; ++a) s += U[IDX(q, a, n_r)] * V[IDX(cc, a, n_c)];
-                    B[IDX(o_qr_r + q, o_up_c + cc, ldb)] += s;
-                }
-            for (int q = 0; q < n_r; ++q)
-                for (int rr = 0; rr < n_c; ++rr) {
-                    double s = 0.0;
-                    for (int a = 0; a < nr; ++a) s += V[IDX(rr, a, n_c)] * U[IDX(q, a, n_r)];
-                    B[IDX(o_up_c + rr, o_qr_r + q, ldb)] += s;
-                }
+    /* QR of the n_r x h block */
+    for (int c = 0; c < h; ++c)
+        for (int r = 0; r < n_r; ++r) Q[IDX(r, c, n_r)] = B[IDX(o_qr_r + r, o_qr_c + c, ldb)];
+    int nr = orc_panel_qr(n_r, h, Q, n_r, U, n_r, T, h);
+    for (int c = 0; c < h; ++c)
+        for (int r = 0; r < n_r; ++r) {
+            B[IDX(o_qr_r + r, o_qr_c + c, ldb)] = Q[IDX(r, c, n_r)];
+            B[IDX(o_qr_c + c, o_qr_r + r, ldb)] = Q[IDX(r, c, n_r)];
         }
+    if (nr > 0) {
+        /* W = B[up cols, qr rows] U T */
+        for (int c = 0; c < nr; ++c)
+            for (int r = 0; r < n_c; ++r) {
+                double s = 0.0;
+                for (int q = 0; q < n_r; ++q) s += B[IDX(o_up_c + r, o_qr_r + q, ldb)] * U[IDX(q, c, n_r)];
+                V[IDX(r, c, n_c)] = s; /* V used as scratch for B U */
+            }
+        for (int c = 0; c < nr; ++c)
+            for (int r = 0; r < n_c; ++r) {
+                double s = 0.0;
+                for (int q = 0; q <= c; ++q) s += V[IDX(r, q, n_c)] * T[IDX(q, c, h)];
+                W[IDX(r, c, n_c)] = s;
+            }
+        /* V = -W */
+        for (int c = 0; c < nr; ++c)
+            for (int r = 0; r < n_c; ++r) V[IDX(r, c, n_c)] = -W[IDX(r, c, n_c)];
+        /* S = U^T W[v rows], Z = T^T S, V[v rows] += 0.5 U Z */
+        for (int c = 0; c < nr; ++c)
+            for (int a = 0; a < nr; ++a) {
+                double s = 0.0;
+                for (int q = 0; q < n_r; ++q) s += U[IDX(q, a, n_r)] * W[IDX(o_v + q, c, n_c)];
+                S[IDX(a, c, h)] = s;
+            }
+        for (int c = 0; c < nr; ++c)
+            for (int a = 0; a < nr; ++a) {
+                double s = 0.0;
+                for (int q = 0; q <= a; ++q) s += T[IDX(q, a, h)] * S[IDX(q, c, h)];
+                Z[IDX(a, c, h)] = s;
+            }
+        for (int c = 0; c < nr; ++c)
+            for (int q = 0; q < n_r; ++q) {
+                double s = 0.0;
+                for (int a = 0; a < nr; ++a) s += U[IDX(q, a, n_r)] * Z[IDX(a, c, h)];
+                V[IDX(o_v + q, c, n_c)] += 0.5 * s;
+            }
+        /* B[qr rows, up cols] += U V^T ; B[up cols, qr rows] += V U^T */
+        for (int cc = 0; cc < n_c; ++cc)
+            for (int q = 0; q < n_r; ++q) {
+                double s = 0.0;
+                for (int a = 0; a < nr; ++a) s += U[IDX(q, a, n_r)] * V[IDX(cc, a, n_c)];
+                B[IDX(o_qr_r + q, o_up_c + cc, ldb)] += s;
+            }
+        for (int q = 0; q < n_r; ++q)
+            for (int rr = 0; rr < n_c; ++rr) {
+                double s = 0.0;
+                for (int a = 0; a < nr; ++a) s += V[IDX(rr, a, n_c)] * U[IDX(q, a, n_r)];
+                B[IDX(o_up_c + rr, o_qr_r + q, ldb)] += s;
+            }
     }
-finished:
     free(Q);
     free(U);
     free(T);
@@ -618,4 +608,68 @@ finished:
     free(V);
     free(S);
     free(Z);
+    return 1;
+}
+
+/*
+ * Algorithm 4.2 in the sequential order it writes: sweeps i = 1, 2, ...
+ * while n - ih >= 2, and within a sweep chases j = 1, 2, ... while the chase
+ * exists (reading A7).  max_chases >= 0 stops after that many chases (to
+ * inspect intermediate fill); max_chases < 0 runs the whole reduction.
+ */
+void orc_band_to_band(int n, double *B, int ldb, int b, int h, int nc_paper, long max_chases)
+{
+    if (h < 1 || b <= h || b % h != 0) return;
+    long done = 0;
+    for (int i = 1; n - i * h >= 2; ++i) {
+        for (int j = 1;; ++j) {
+            if (max_chases >= 0 && done >= max_chases) return;
+            if (!orc_chase(n, B, ldb, b, h, i, j, nc_paper)) break;
+            ++done;
+        }
+    }
+}
+
+typedef struct {
+    long key;
+    int i, j;
+} orc_chase_id;
+
+static int cmp_chase(const void *a, const void *b)
+{
+    const orc_chase_id *x = (const orc_chase_id *)a, *y = (const orc_chase_id *)b;
+    if (x->key != y->key) return (x->key > y->key) - (x->key < y->key);
+    return (x->i > y->i) - (x->i < y->i);
+}
+
+/*
+ * The same chases as orc_band_to_band, executed in wavefront order: chase
+ * (i, j) gets the time step t = wave * i + j, and chases of one time step
+ * run in increasing i (tie_desc = 0) or decreasing i (tie_desc != 0).
+ * A pipelined schedule is legal exactly when every such order reproduces
+ * the sequential result bit for bit.  (The pipeline the paper pictures
+ * for k = 2 corresponds to wave = 2.)
+ */
+void orc_band_to_band_wavefront(int n, double *B, int ldb, int b, int h, int wave, int tie_desc)
+{
+    if (h < 1 || b <= h || b % h != 0) return;
+    long cnt = 0, cap = 1024;
+    orc_chase_id *ids = (orc_chase_id *)malloc(sizeof(orc_chase_id) * (size_t)cap);
+    for (int i = 1; n - i * h >= 2; ++i)
+        for (int j = 1; n - ((i - 1) * h + (j - 1) * b + h) >= 2; ++j) {
+            if (cnt == cap) {
+                cap *= 2;
+                ids = (orc_chase_id *)realloc(ids, sizeof(orc_chase_id) * (size_t)cap);
+            }
+            ids[cnt].key = (long)wave * i + j;
+            ids[cnt].i = tie_desc ? -i : i;
+            ids[cnt].j = j;
+            ++cnt;
+        }
+    qsort(ids, (size_t)cnt, sizeof(orc_chase_id), cmp_chase);
+    for (long k = 0; k < cnt; ++k) {
+        int i = ids[k].i < 0 ? -ids[k].i : ids[k].i;
+        orc_chase(n, B, ldb, b, h, i, ids[k].j, 0);
+    }
+    free(ids);
 }

@@ -308,3 +308,17 @@ def test_band_schedule(orc):
     assert orc.band_schedule(32) == [32, 16, 8, 4, 2, 1]
     assert orc.band_schedule(6) == [6, 3, 1]
     assert orc.band_schedule(1) == [1]
+
+
+@pytest.mark.parametrize("n,b,h", [(64, 8, 4), (61, 6, 3), (50, 8, 2), (45, 8, 1), (70, 16, 8), (30, 2, 1)])
+def test_band_to_band_wavefront_legality(orc, n, b, h):
+    """Chase (i, j) conflicts with (i-1, j+2): the pipeline t = 2i + j that
+    the Fig. 2 caption pictures depends on the order inside a time step,
+    while t = 3i + j (chase (i, j) waits for (i-1, j+2)) reproduces the
+    sequential order of Algorithm 4.2 bit for bit in either tie order."""
+    A = I.random_band(n, b, 5000 + n + b)
+    seq = orc.band_to_band(A, b, h)
+    for tie in (False, True):
+        np.testing.assert_array_equal(orc.band_to_band_wavefront(A, b, h, 3, tie), seq)
+    two = [np.array_equal(orc.band_to_band_wavefront(A, b, h, 2, tie), seq) for tie in (False, True)]
+    assert not all(two)
