@@ -1,0 +1,454 @@
+#!/usr/bin/env python
+"""Benchmark: eigvalsh TFLOP/s (nominal 4n^3/3 flops) on one GB300.
+
+Workload (default): n = 16384, mixed precision (FP32 data, tensor-core
+trailing update, FP64 Householder norms/tau/beta and FP64 Sturm recurrence),
+A = Q diag(D) Q^T with D geometrically spaced over 1e-6..1 in magnitude with
+random signs and 16-fold clusters of gap 1e-10, Q from the QR of a seeded
+N(0,1) matrix; first half-bandwidth b0 = 128, halvings 128 -> ... -> 1.
+A step is one sev_eigvalsh call (full-to-band, every band halving,
+bisection).  The FP64 form of the same matrix is timed beside it.
+
+Output: one JSON line on rank 0 (see the keys below).  --impl reference
+times the CPU oracle on a bounded sample of the same workload instead.
+Multi-GPU (torchrun): independent replicas, one matrix per rank (the
+single-matrix path does not shard); value aggregates all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "eigvalsh TFLOP/s (4n^3/3 nominal) at n=16384, mixed precision"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=16384)
+    p.add_argument("--b0", type=int, default=128)
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64-form timing")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ helpers
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock / power / throttle reasons."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def nominal_flops(n):
+    return 4.0 * n ** 3 / 3.0
+
+
+def panel_sizes(n, b):
+    out = []
+    k = 0
+    while True:
+        r0 = (k + 1) * b
+        if r0 >= n or n - r0 < 2:
+            break
+        out.append(n - r0)
+        k += 1
+    return out
+
+
+def schedule(b0):
+    s = [b0]
+    while s[-1] > 1:
+        b = s[-1]
+        s.append(b // 2 if b % 2 == 0 else 1)
+    return s
+
+
+def kernel_model(name, n, b0, elem):
+    """Algorithmic work of one step for a kernel: (amount, unit, bound)."""
+    Ns = panel_sizes(n, b0)
+    if name in ("syr2k", "syr2k_tc"):
+        flops = sum(2.0 * N * (N + 1) * b0 for N in Ns)
+        return flops, "flop", "tensor" if name.endswith("_tc") else "alu"
+    if name in ("symm", "symm_tc"):
+        flops = sum(2.0 * N * N * b0 for N in Ns)
+        return flops, "flop", "tensor" if name.endswith("_tc") else "alu"
+    if name == "band_chase":
+        # one read + one write of the active band per sweep (k = 2 halvings):
+        # 2 k s n^2 bytes per stage
+        stages = len(schedule(b0)) - 1
+        return stages * 2 * 2 * elem * float(n) ** 2, "byte", "hbm"
+    if name == "bisect":
+        # Sturm steps (one FP64 division each): n eigenvalues x ~iterations x n
+        rtol = 1e-9 if elem == 4 else 1e-14
+        iters = math.ceil(math.log2(2.0 / rtol)) + 1
+        return float(n) * n * iters, "sturm_step", "alu"
+    return None, None, None
+
+
+def roofline(name, amount, unit, bound, ms_per_step, peaks, clocks, elem):
+    if amount is None or ms_per_step <= 0:
+        return None
+    sec = ms_per_step / 1e3
+    mhz = (clocks or {}).get("sm_mhz") or 1900.0
+    if unit == "flop" and bound == "tensor":
+        bf16 = peaks.get("bf16_tflops_sustained") or 1713.1
+        peak = bf16 / 3.0  # BF16x3: three bf16 products per useful FP32-class product
+        ach = amount / sec / 1e12
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_note": "of measured: bf16 sustained / 3 (BF16x3 useful flops)"}
+    if unit == "flop":
+        # SIMT FMA: FP32 152 SMs x 128 FMA/clk x 2; FP64 152 x 2 DFMA/clk x 2
+        per_clk = 152 * (128 if elem == 4 else 2) * 2
+        peak = per_clk * mhz * 1e6 / 1e12
+        ach = amount / sec / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "peak_note": "unit counts x median SM clock"}
+    if unit == "byte":
+        peak = peaks.get("hbm_gbs") or 6762.3
+        ach = amount / sec / 1e9
+        return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_note": "of measured"}
+    if unit == "sturm_step":
+        # one IEEE FP64 division per step; 59.66 G div/s measured on this GB300 at ~1995 MHz
+        peak = 59.66 * mhz / 1995.0
+        ach = amount / sec / 1e9
+        return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gstep/s", "frac": ach / peak,
+                "peak_note": "FP64 divide throughput (microbenchmark), clock-scaled"}
+    return None
+
+
+# ---------------------------------------------------------------- oracle leg
+def oracle_sample(A64_host, n, rtol, seconds, steps_cap=None):
+    """Time the CPU oracle on a bounded sample of the workload and
+    extrapolate: the first m Householder steps of the tridiagonalisation of
+    A (step j costs ~(n-1-j)^2) and k of the n bisections (equal cost each)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    budget_tri = 0.8 * seconds
+    # per-step estimate from one step
+    M = np.asfortranarray(A64_host.T)  # symmetric: the transpose is the same matrix, F-ordered view
+    M = np.array(M, order="F", copy=True)
+    d = np.zeros(n)
+    e = np.zeros(n)
+    t0 = time.perf_counter()
+    oracle.tridiagonalize_inplace(M, d, e, 1)
+    t1 = time.perf_counter() - t0
+    m = max(1, min(n - 2, int(budget_tri / max(t1, 1e-6))))
+    if steps_cap:
+        m = min(m, steps_cap)
+    M = np.array(np.asfortranarray(A64_host.T), order="F", copy=True)
+    t0 = time.perf_counter()
+    oracle.tridiagonalize_inplace(M, d, e, m)
+    t_m = time.perf_counter() - t0
+    del M
+    w = (np.arange(n - 1, 1, -1, dtype=np.float64)) ** 2  # (n-1-j)^2, j = 0..n-3
+    t_tri = t_m * w.sum() / w[:m].sum()
+    rng = np.random.default_rng(1)
+    dd, ee = rng.standard_normal(n), rng.standard_normal(n - 1)
+    k = 8
+    t0 = time.perf_counter()
+    oracle.bisect_range(dd, ee, 0, k, rtol)
+    tk = time.perf_counter() - t0
+    k = max(8, min(n, int(0.2 * seconds / max(tk / 8, 1e-9))))
+    t0 = time.perf_counter()
+    oracle.bisect_range(dd, ee, n // 2 - k // 2, n // 2 - k // 2 + k, rtol)
+    t_k = time.perf_counter() - t0
+    t_bis = t_k * n / k
+    total = t_tri + t_bis
+    return {
+        "seconds_extrapolated": total,
+        "value": nominal_flops(n) / total / 1e12,
+        "sample": "first %d of %d Householder steps of the oracle tridiagonalisation of the workload matrix "
+                  "(%.2f s, extrapolated by (n-1-j)^2) + %d of %d bisections (rtol %.0e, %.2f s, x n/k)"
+                  % (m, n - 2, t_m, k, n, rtol, t_k),
+        "measured_seconds": t_m + t_k,
+    }
+
+
+def gen_workload(n, device):
+    import torch
+
+    from paper_1604_03703_gb300 import inputs as I
+
+    D = I.workload_clustered_d(n)
+    A64 = I.qdq_torch(D, I.SEED_BASE + 2, device)
+    torch.cuda.synchronize()
+    return A64, D
+
+
+# ------------------------------------------------------------------- arms
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+
+    n = args.n
+    torch.cuda.set_device(local)
+    A64, D = gen_workload(n, "cuda:%d" % local)
+    A_host = A64.cpu().numpy()
+    del A64
+    torch.cuda.empty_cache()
+    rtol = 1e-9
+    per = max(2.0, min(args.cpu_seconds, 20.0) / 3)
+    vals, last = [], None
+    for s in range(args.warmup + args.steps):
+        r = oracle_sample(A_host, n, rtol, per)
+        if s >= args.warmup:
+            vals.append(r["value"])
+            last = r
+    value = statistics.median(vals)
+    ms = nominal_flops(n) / (value * 1e12) * 1e3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "eigvalsh n=%d clustered QDQ^T spectrum (CPU oracle, bounded sample)" % n,
+                   "n": n, "b0": args.b0},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_1604_03703_gb300 import api
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = "cuda:%d" % local
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device(device))
+    n, b0 = args.n, args.b0
+    A64, D = gen_workload(n, device)
+    Dmax = float(np.abs(D).max())
+    A_host64 = A64.cpu().numpy() if rank == 0 else None
+    A0 = A64.float()
+    if args.no_fp64:
+        del A64
+        A64 = None
+    torch.cuda.empty_cache()
+    A = torch.empty_like(A0)
+    h = api.Handle(local)
+    lam = torch.empty(n, dtype=torch.float64, device=device)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # warm-up
+    for _ in range(max(args.warmup, 3)):
+        A.copy_(A0)
+        h.eigvalsh(A, b0, out=lam)
+    torch.cuda.synchronize()
+    h.raise_device_error("warm-up")
+    # one untimed profiling step: per-kernel totals and launch counts
+    h.set_kernel_timing(True)
+    A.copy_(A0)
+    h.eigvalsh(A, b0, out=lam)
+    prof = h.kernel_times()
+    h.set_kernel_timing(False)
+    launches_per_step = sum(c for _, c in prof.values())
+    dominant = max(prof, key=lambda k: prof[k][0])
+
+    # timed region: K steps; only the dominant kernel's launches are bracketed
+    h.set_kernel_timing(dominant)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    for s in range(args.steps):
+        A.copy_(A0)  # restore the input the previous step overwrote (outside the step's events)
+        ev[s][0].record()
+        h.eigvalsh(A, b0, out=lam)
+        ev[s][1].record()
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    dom_ms, dom_cnt = h.kernel_times().get(dominant, (0.0, 0))
+    h.set_kernel_timing(False)
+    h.raise_device_error("timed steps")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([tot_ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * nominal_flops(n) / (ms_per_step / 1e3) / 1e12
+    lam_np = lam.cpu().numpy()
+    err = float(np.abs(np.sort(lam_np) - D).max() / Dmax)
+
+    # end to end through the host-buffer entry point (H2D + solve + D2H)
+    e2e = None
+    if not args.no_e2e:
+        A_pin = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+        A_pin.copy_(A0.cpu())
+        out = torch.empty(n, dtype=torch.float64)
+        h.eigvalsh_host(A_pin, b0, out=out)  # warm (allocates the staging buffer)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h.eigvalsh_host(A_pin, b0, out=out)
+        dt = (time.perf_counter() - t0) / args.steps
+        e2e = {"value": world * nominal_flops(n) / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 4 * n * n, "d2h_bytes_per_step": 8 * n, "ms_per_step": dt * 1e3}
+        del A_pin
+
+    # the FP64 form on the same matrix (one warm-up + one timed call)
+    fp64 = None
+    if A64 is not None:
+        del A0, A
+        torch.cuda.empty_cache()
+        A = torch.empty_like(A64)
+        A.copy_(A64)
+        h.eigvalsh(A, 64, out=lam)
+        torch.cuda.synchronize()
+        A.copy_(A64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.eigvalsh(A, 64, out=lam)
+        e1.record()
+        torch.cuda.synchronize()
+        h.raise_device_error("fp64")
+        f_ms = e0.elapsed_time(e1)
+        f_err = float(np.abs(np.sort(lam.cpu().numpy()) - D).max() / Dmax)
+        fp64 = {"eigvalsh_s": f_ms / 1e3, "tflops": nominal_flops(n) / (f_ms / 1e3) / 1e12, "b0": 64,
+                "max_err_vs_D": f_err, "mixed_speedup": f_ms / ms_per_step}
+
+    peaks = measured_peaks()
+    amount, unit, bound = kernel_model(dominant, n, b0, 4)
+    dom_ms_step = dom_ms / args.steps if dom_ms else prof[dominant][0]
+    roof = roofline(dominant, amount, unit, bound, dom_ms_step, peaks, clk, 4)
+    if roof is not None:
+        roof["kernel"] = dominant
+        roof["traffic"] = None
+        roof["launches_per_step"] = prof[dominant][1]
+        roof["ms_per_step"] = dom_ms_step
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cpu = oracle_sample(A_host64, n, 1e-9, args.cpu_seconds)
+        cpu = {"value": cpu["value"], "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": cpu["sample"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+bf16x3 (f64 norms, f64 Sturm)", "data": "synthetic",
+        "config": {"workload": "eigvalsh n=%d, A = Q diag(D) Q^T, D geometric 1e-6..1 with random signs and "
+                               "16-fold clusters (gap 1e-10), FP32 data, b0=%d halving to 1" % (n, b0),
+                   "n": n, "b0": b0, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (1 GiB matrix per step); input restore excluded from step events"},
+        "max_err_vs_D": err,
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "fp64": fp64,
+        "kernels_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,173 @@
+/*
+ * sev.h -- C ABI of the GB300 (sm_103a) symmetric eigenvalue library.
+ *
+ * The library computes the eigenvalues of a dense real symmetric matrix by
+ * the successive band reduction of Solomonik, Ballard, Demmel and Hoefler,
+ * "A communication-avoiding parallel algorithm for the symmetric eigenvalue
+ * problem" (arXiv 1604.03703), on one GPU:
+ *
+ *   full-to-band    Algorithm 4.1 (tree QR of each panel, Algorithm 3.2;
+ *                   compact-WY by Householder reconstruction, Cor. 3.7;
+ *                   two-sided trailing update, Eq. 4.1)
+ *   band-to-band    Algorithm 4.2 (bulge chasing, b -> h), repeated
+ *                   b0 -> b0/2 -> ... -> 1 as in Algorithm 4.3
+ *   tridiag_bisect  eigenvalues of the final tridiagonal by Sturm-count
+ *                   bisection (the "compute its eigenvalues" step of
+ *                   Algorithm 4.3)
+ *
+ * Conventions for every entry point:
+ *  - Matrices are column-major.  Only the LOWER triangle of a symmetric input
+ *    is read (the paper stores A "as a nonsymmetric matrix"; we read half).
+ *  - Pointers are DEVICE pointers unless a name ends in _host.  The caller
+ *    owns every buffer it passes; the library never frees them.
+ *  - Inputs named A / AB are overwritten (LAPACK-style workspace semantics).
+ *  - Calls are asynchronous on the handle's stream (sev_set_stream); a
+ *    return of SEV_OK means the work was enqueued.  Errors detected on the
+ *    device (a wait that timed out, a bisection that did not converge) are
+ *    latched in the handle and returned by sev_get_error().
+ *  - Precision: SEV_FP64 -- data double, all arithmetic FP64.
+ *    SEV_MIXED -- data float (FP32); the trailing update runs as BF16x3
+ *    split products on the tensor cores with FP32 accumulation; Householder
+ *    norms, tau and beta are computed in FP64; the Sturm recurrence of the
+ *    bisection is FP64; eigenvalues are returned as double.
+ *  - Return codes: SEV_OK = 0; a negative value -i means argument i (1-based,
+ *    the handle counts as argument 1) is invalid; positive values are the
+ *    SEV_ERR_* codes below.
+ *
+ * Band storage ("packed lower band"): a symmetric matrix with half-bandwidth
+ * b (a_ij = 0 for |i - j| > b) is held in an ldab x n column-major array AB
+ * with AB[d + j*ldab] = A(j + d, j) for 0 <= d < ldab and j + d < n; the
+ * remaining entries are zero.  Band-to-band needs ldab >= 2b because the
+ * bulges of Algorithm 4.2 reach 2b-1 below the diagonal.
+ */
+#ifndef SEV_H
+#define SEV_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sev_ctx *sev_handle;
+
+typedef enum {
+    SEV_FP64 = 0,  /* double data, FP64 arithmetic throughout */
+    SEV_MIXED = 1  /* float data, BF16x3 tensor-core update, FP64 norms/tau/beta and Sturm */
+} sev_prec;
+
+enum {
+    SEV_OK = 0,
+    SEV_ERR_NONFINITE = 1,  /* input holds NaN or Inf */
+    SEV_ERR_NOCONV = 2,     /* bisection hit its iteration cap */
+    SEV_ERR_TIMEOUT = 3,    /* a device-side wait hit its iteration cap */
+    SEV_ERR_CUDA = 4,       /* a CUDA runtime call failed */
+    SEV_ERR_WORKSPACE = 5,  /* caller workspace too small / allocation failed */
+    SEV_ERR_UNSUPPORTED = 6, /* parameter combination not supported */
+    SEV_ERR_INTERNAL = 7     /* a kernel's self-check found an index outside its buffer */
+};
+
+/* Create a handle bound to CUDA device `device`; the stream defaults to the
+ * legacy default stream.  Returns SEV_ERR_CUDA if the device is unusable. */
+int sev_create(sev_handle *handle, int device);
+
+/* Destroy the handle and the workspace it allocated itself.  Does not
+ * synchronise; the caller must not destroy a handle with work in flight. */
+int sev_destroy(sev_handle handle);
+
+/* Set the CUDA stream (a cudaStream_t passed as void*) for later calls. */
+int sev_set_stream(sev_handle handle, void *stream);
+
+/* Bytes of device workspace that sev_eigvalsh(n, b0, prec) needs. */
+int sev_workspace_query(sev_handle handle, int n, int b0, int prec, size_t *bytes);
+
+/* Give the handle a caller-owned device workspace of `bytes` bytes (at least
+ * 256-byte aligned).  Later calls use it instead of allocating; calls whose
+ * workspace need exceeds it return SEV_ERR_WORKSPACE.  NULL/0 reverts to
+ * library-owned workspace (allocated on demand with cudaMalloc). */
+int sev_set_workspace(sev_handle handle, void *workspace, size_t bytes);
+
+/*
+ * Eigenvalues of the symmetric n x n matrix A (Algorithm 4.3):
+ * full-to-band to half-bandwidth b0, halvings b0 -> ... -> 1, bisection.
+ *   A      device, n x n, leading dimension lda >= max(1, n); double for
+ *          SEV_FP64, float for SEV_MIXED; lower triangle read, overwritten.
+ *   b0     first half-bandwidth, 1 <= b0 (values >= n-1 skip full-to-band);
+ *          0 picks the library's default for (n, prec).
+ *   eigs   device, n doubles, ascending on completion.
+ * Bisection tolerance: relative 1e-14 (SEV_FP64) or 1e-9 (SEV_MIXED) of the
+ * Gershgorin bound of the tridiagonal.
+ */
+int sev_eigvalsh(sev_handle handle, int n, void *A, int lda, int b0, int prec, double *eigs);
+
+/* sev_eigvalsh with HOST buffers: copies A_host (n x n, lda, float or double
+ * by prec, not modified) to device workspace, runs sev_eigvalsh, copies the
+ * eigenvalues back to eigs_host and synchronises the stream.  Page-locked
+ * host memory makes the copies asynchronous DMA. */
+int sev_eigvalsh_host(sev_handle handle, int n, const void *A_host, int lda, int b0, int prec,
+                      double *eigs_host);
+
+/*
+ * Full-to-band reduction (Algorithm 4.1, run right-looking): per panel of b
+ * columns, tree QR of the trailing N x b panel (Algorithm 3.2), Householder
+ * reconstruction of (U, T) (Cor. 3.7), W = A22 U, V from the V_1 formula,
+ * A22 <- A22 + U V^T + V U^T (Eq. 4.1), band block <- S R.
+ *   A     device, n x n (lda), lower triangle read; on return A's lower
+ *         triangle holds the band matrix (exact zeros below the band).
+ *   b     half-bandwidth >= 1 (b >= n-1 only copies the band).
+ *   AB    device, packed lower band, ldab >= b+1; receives the band matrix.
+ */
+int sev_full_to_band(sev_handle handle, int n, void *A, int lda, int b, int prec, void *AB, int ldab);
+
+/*
+ * Band-to-band reduction b -> h (Algorithm 4.2) in place on packed band
+ * storage.  Requires h >= 1, h < b, b % h == 0, ldab >= 2b.  Entries of AB
+ * at distance > b from the diagonal must be zero on entry; on return the
+ * band has half-bandwidth h and entries beyond it are zero.  Chases run as a
+ * persistent wavefront in which chase (i, j) starts once chase (i-1, j+2)
+ * and (i, j-1) are complete.
+ */
+int sev_band_to_band(sev_handle handle, int n, void *AB, int ldab, int b, int h, int prec);
+
+/*
+ * All eigenvalues of the symmetric tridiagonal T with diagonal d[0..n-1] and
+ * off-diagonal e[0..n-2] (device, double), ascending, into eigs (device,
+ * n doubles), by bisection on the Sturm count (negative pivots of
+ * LDL^T(T - xI) with the pivmin guard) from the Gershgorin interval, until
+ * hi - lo <= max(rtol*max(|lo|,|hi|), rtol*||T||_G) (rtol > 0).
+ */
+int sev_tridiag_bisect(sev_handle handle, int n, const double *d, const double *e, double rtol,
+                       double *eigs);
+
+/* Copy the diagonal and first subdiagonal of a packed band (float or double
+ * by prec) into FP64 device arrays d (n) and e (n-1). */
+int sev_band_tridiag_extract(sev_handle handle, int n, const void *AB, int ldab, int prec, double *d,
+                             double *e);
+
+/* Synchronise the handle's stream and return (and clear) the first error
+ * latched by device code since the last call, or SEV_OK. */
+int sev_get_error(sev_handle handle);
+
+/* Human-readable text of a return code. */
+const char *sev_status_string(int code);
+
+/*
+ * Per-kernel timing for roofline reports.  Every launch of a library kernel
+ * whose id k has bit k set in `mask` is bracketed by CUDA events on the
+ * handle's stream; totals are read back per kernel id (see sev_kernel_name).
+ * mask = 0 disables timing (the default); ~0ULL times every kernel.
+ */
+int sev_set_kernel_timing(sev_handle handle, unsigned long long mask);
+/* Number of kernel ids. */
+int sev_kernel_count(void);
+/* Name of kernel id k (0 <= k < sev_kernel_count()). */
+const char *sev_kernel_name(int k);
+/* Synchronises; total milliseconds and launch count of kernel id k since
+ * timing was enabled or last reset; reset != 0 clears the totals after. */
+int sev_kernel_time(sev_handle handle, int k, double *total_ms, long *launches, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SEV_H */

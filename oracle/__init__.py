@@ -61,6 +61,8 @@ def _load():
             lib.orc_gershgorin.argtypes = [i, _dp, _dp, d, _dp, _dp]
             lib.orc_bisect.restype = i
             lib.orc_bisect.argtypes = [i, _dp, _dp, d, i, _dp]
+            lib.orc_bisect_range.restype = i
+            lib.orc_bisect_range.argtypes = [i, _dp, _dp, d, i, i, i, _dp]
             lib.orc_eigvalsh.restype = i
             lib.orc_eigvalsh.argtypes = [i, _dp, i, d, _dp]
             lib.orc_jacobi.restype = i
@@ -151,6 +153,17 @@ def bisect(d, e, rtol: float = 1e-14, maxit: int = 200, return_noconv: bool = Fa
     out = np.zeros(max(n, 1))
     nc = _load().orc_bisect(n, _ptr(d), _ptr(ee), float(rtol), int(maxit), _ptr(out))
     return (out[:n], nc) if return_noconv else out[:n]
+
+
+def bisect_range(d, e, k0: int, k1: int, rtol: float = 1e-14, maxit: int = 200):
+    """Eigenvalues k0 <= k < k1 (ascending indices) of T(d, e) by bisection."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = d.size
+    ee = np.zeros(max(n, 1))
+    ee[: n - 1] = np.asarray(e, dtype=np.float64)[: n - 1]
+    out = np.zeros(max(k1 - k0, 1))
+    _load().orc_bisect_range(n, _ptr(d), _ptr(ee), float(rtol), int(maxit), int(k0), int(k1), _ptr(out))
+    return out[: k1 - k0]
 
 
 def eigvalsh(A, rtol: float = 1e-14):

@@ -200,11 +200,22 @@ double orc_gershgorin(int n, const double *d, const double *e, double pivmin,
  * mid no longer splits the interval, or after maxit steps; eig = 0.5*(lo+hi).
  * Returns the number of eigenvalues that hit maxit before converging.
  */
+int orc_bisect_range(int n, const double *d, const double *e, double rtol, int maxit, int k0, int k1,
+                     double *eigs);
+
 int orc_bisect(int n, const double *d, const double *e, double rtol, int maxit, double *eigs)
+{
+    return orc_bisect_range(n, d, e, rtol, maxit, 0, n, eigs);
+}
+
+/* Bisection for eigenvalue indices k0 <= k < k1 only (eigs[k - k0]); the
+ * same per-index procedure as orc_bisect (used to time a bounded sample). */
+int orc_bisect_range(int n, const double *d, const double *e, double rtol, int maxit, int k0, int k1,
+                     double *eigs)
 {
     if (n <= 0) return 0;
     if (n == 1) {
-        eigs[0] = d[0];
+        if (k0 == 0 && k1 > 0) eigs[0] = d[0];
         return 0;
     }
     double *e2 = (double *)malloc(sizeof(double) * (size_t)n);
@@ -215,7 +226,7 @@ int orc_bisect(int n, const double *d, const double *e, double rtol, int maxit, 
     double tnorm = orc_gershgorin(n, d, e, pivmin, &gl, &gu);
     double atol = rtol * tnorm;
     int noconv = 0;
-    for (int k = 0; k < n; ++k) {
+    for (int k = k0; k < k1; ++k) {
         double lo = gl, hi = gu;
         int it = 0;
         for (;;) {
@@ -236,7 +247,7 @@ int orc_bisect(int n, const double *d, const double *e, double rtol, int maxit, 
                 lo = mid;
             ++it;
         }
-        eigs[k] = 0.5 * (lo + hi);
+        eigs[k - k0] = 0.5 * (lo + hi);
     }
     free(e2);
     return noconv;

@@ -1,0 +1,414 @@
+// api.cu -- the C ABI (include/sev.h): handle, workspace, argument checks,
+// per-kernel timing, and the eigvalsh driver that chains the stages of
+// Algorithm 4.3: full-to-band, band halvings b0 -> b0/2 -> ... -> 1, and
+// bisection on the final tridiagonal.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace sev {
+
+const char *const kKernelNames[K_COUNT] = {
+    "bisect_prep",  "bisect",       "band_from_dense", "tridiag_extract", "band_chase",
+    "tsqr_leaf_qr", "tsqr_node_qr", "tsqr_node_apply", "tsqr_leaf_apply", "recon_lu",
+    "recon_u2",     "symm",         "vform_xt",        "vform_utx",       "vform_reduce",
+    "vform_v",      "syr2k",        "split_bf16",      "syr2k_tc",        "symm_tc",
+    "misc"};
+
+static cudaEvent_t pool_get(sev_ctx *h) {
+    if (!h->event_pool.empty()) {
+        cudaEvent_t e = h->event_pool.back();
+        h->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void timing_begin(sev_ctx *h, int kid) {
+    if (!((h->timing >> kid) & 1ULL)) return;
+    TimedLaunch t;
+    t.kid = kid;
+    t.e0 = pool_get(h);
+    t.e1 = pool_get(h);
+    cudaEventRecord(t.e0, h->stream);
+    h->pending.push_back(t);
+}
+
+void timing_end(sev_ctx *h, int kid) {
+    if (!((h->timing >> kid) & 1ULL) || h->pending.empty()) return;
+    TimedLaunch &t = h->pending.back();
+    if (t.kid == kid) cudaEventRecord(t.e1, h->stream);
+}
+
+int check_launch(sev_ctx *) {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SEV_OK : SEV_ERR_CUDA;
+}
+
+static void drain_timing(sev_ctx *h) {
+    for (TimedLaunch &t : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.e0, t.e1) == cudaSuccess) {
+            h->tot_ms[t.kid] += ms;
+            h->launches[t.kid] += 1;
+        }
+        h->event_pool.push_back(t.e0);
+        h->event_pool.push_back(t.e1);
+    }
+    h->pending.clear();
+}
+
+int get_workspace(sev_ctx *h, size_t bytes, void **out) {
+    if (h->ws_ext) {
+        if (h->ws_ext_bytes < bytes) return SEV_ERR_WORKSPACE;
+        *out = h->ws_ext;
+        return SEV_OK;
+    }
+    if (h->ws_own_bytes < bytes) {
+        if (h->ws_own) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->ws_own);
+            h->ws_own = nullptr;
+            h->ws_own_bytes = 0;
+        }
+        if (cudaMalloc(&h->ws_own, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return SEV_ERR_WORKSPACE;
+        }
+        h->ws_own_bytes = bytes;
+    }
+    *out = h->ws_own;
+    return SEV_OK;
+}
+
+static int default_b0(int n, int prec) {
+    if (prec == SEV_FP64) return n >= 4096 ? 64 : 32;
+    return n >= 12288 ? 128 : (n >= 1024 ? 64 : 32);
+}
+
+static int schedule(int b0, int *out) {
+    int k = 0;
+    out[k++] = b0;
+    while (out[k - 1] > 1) {
+        const int b = out[k - 1];
+        out[k++] = (b % 2 == 0) ? b / 2 : 1;
+    }
+    return k;
+}
+
+template <typename T>
+static size_t eig_workspace(sev_ctx *h, int n, int b0) {
+    int sched[40];
+    const int ns = schedule(b0, sched);
+    const int ldab = 2 * b0 > 2 ? 2 * b0 : 2;
+    size_t stage = bisect_workspace(n);
+    if (b0 < n - 1) {
+        const size_t f = full_to_band_workspace<T>(h, n, b0);
+        if (f > stage) stage = f;
+    }
+    for (int s = 0; s + 1 < ns; ++s) {
+        const size_t w = band_workspace(n, sched[s], sched[s + 1]);
+        if (w > stage) stage = w;
+    }
+    Carver c(nullptr);
+    c.take<T>((size_t)ldab * n);
+    c.take<double>((size_t)n);
+    c.take<double>((size_t)n);
+    c.take<char>(stage);
+    return c.bytes();
+}
+
+template <typename T>
+static int eigvalsh_t(sev_ctx *h, int n, T *A, int lda, int b0, double *eigs) {
+    if (b0 > n - 1) b0 = n - 1 > 1 ? n - 1 : 1;
+    int sched[40];
+    const int ns = schedule(b0, sched);
+    for (int s = 0; s + 1 < ns; ++s)
+        if (band_smem_bytes<T>(sched[s], sched[s + 1]) > h->smem_optin) return SEV_ERR_UNSUPPORTED;
+    const int ldab = 2 * b0 > 2 ? 2 * b0 : 2;
+    void *ws = nullptr;
+    const size_t need = eig_workspace<T>(h, n, b0);
+    int rc = get_workspace(h, need, &ws);
+    if (rc) return rc;
+    Carver c(ws);
+    T *AB = c.take<T>((size_t)ldab * n);
+    double *d = c.take<double>((size_t)n);
+    double *e = c.take<double>((size_t)n);
+    const size_t stage_bytes = need - c.bytes();
+    void *stage = c.take<char>(stage_bytes);
+    if (b0 < n - 1) {
+        rc = launch_full_to_band<T>(h, n, A, lda, b0, AB, ldab, stage, stage_bytes);
+    } else {
+        rc = launch_band_from_dense<T>(h, n, A, lda, b0, AB, ldab);
+    }
+    if (rc) return rc;
+    for (int s = 0; s + 1 < ns; ++s) {
+        rc = launch_band_to_band<T>(h, n, AB, ldab, sched[s], sched[s + 1], stage, stage_bytes);
+        if (rc) return rc;
+    }
+    rc = launch_tridiag_extract<T>(h, n, AB, ldab, d, e);
+    if (rc) return rc;
+    const double rtol = sizeof(T) == 8 ? 1e-14 : 1e-9;
+    return launch_bisect(h, n, d, e, rtol, eigs, stage, stage_bytes);
+}
+
+}  // namespace sev
+
+using namespace sev;
+
+extern "C" {
+
+int sev_create(sev_handle *handle, int device) {
+    if (!handle) return -1;
+    *handle = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return device < 0 ? -2 : SEV_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return SEV_ERR_CUDA;
+    sev_ctx *h = new (std::nothrow) sev_ctx();
+    if (!h) return SEV_ERR_WORKSPACE;
+    h->device = device;
+    cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    h->smem_optin = (size_t)optin;
+    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) {
+        delete h;
+        return SEV_ERR_CUDA;
+    }
+    cudaMemset(h->d_err, 0, sizeof(int));
+    if (const char *v = getenv("SEV_LEAF_ROWS")) h->leaf_rows_override = atoi(v);
+    *handle = h;
+    return SEV_OK;
+}
+
+int sev_destroy(sev_handle h) {
+    if (!h) return -1;
+    for (TimedLaunch &t : h->pending) {
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+    if (h->ws_own) cudaFree(h->ws_own);
+    if (h->h_stage) cudaFree(h->h_stage);
+    if (h->d_err) cudaFree(h->d_err);
+    delete h;
+    return SEV_OK;
+}
+
+int sev_set_stream(sev_handle h, void *stream) {
+    if (!h) return -1;
+    h->stream = (cudaStream_t)stream;
+    return SEV_OK;
+}
+
+int sev_workspace_query(sev_handle h, int n, int b0, int prec, size_t *bytes) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (b0 < 0) return -3;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -4;
+    if (!bytes) return -5;
+    if (n == 0) {
+        *bytes = 0;
+        return SEV_OK;
+    }
+    if (b0 == 0) b0 = default_b0(n, prec);
+    if (b0 > n - 1) b0 = n - 1 > 1 ? n - 1 : 1;
+    *bytes = prec == SEV_FP64 ? eig_workspace<double>(h, n, b0) : eig_workspace<float>(h, n, b0);
+    return SEV_OK;
+}
+
+int sev_set_workspace(sev_handle h, void *ws, size_t bytes) {
+    if (!h) return -1;
+    if (ws && ((uintptr_t)ws & 255)) return -2;
+    h->ws_ext = bytes ? ws : nullptr;
+    h->ws_ext_bytes = ws ? bytes : 0;
+    return SEV_OK;
+}
+
+int sev_eigvalsh(sev_handle h, int n, void *A, int lda, int b0, int prec, double *eigs) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && !A) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (b0 < 0) return -5;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -6;
+    if (n > 0 && !eigs) return -7;
+    if (n == 0) return SEV_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    if (b0 == 0) b0 = default_b0(n, prec);
+    if (n == 1) {
+        // a 1 x 1 matrix: its entry is the eigenvalue
+        if (prec == SEV_FP64) {
+            SEV_CUDA(cudaMemcpyAsync(eigs, A, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+            return SEV_OK;
+        }
+        return launch_tridiag_extract<float>(h, 1, (const float *)A, 1, eigs, eigs);
+    }
+    return prec == SEV_FP64 ? eigvalsh_t<double>(h, n, (double *)A, lda, b0, eigs)
+                            : eigvalsh_t<float>(h, n, (float *)A, lda, b0, eigs);
+}
+
+int sev_eigvalsh_host(sev_handle h, int n, const void *A_host, int lda, int b0, int prec, double *eigs_host) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && !A_host) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (b0 < 0) return -5;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -6;
+    if (n > 0 && !eigs_host) return -7;
+    if (n == 0) return SEV_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    const size_t es = prec == SEV_FP64 ? sizeof(double) : sizeof(float);
+    const size_t abytes = ((es * (size_t)n * n + 255) & ~(size_t)255);
+    const size_t need = abytes + sizeof(double) * (size_t)n;
+    if (h->h_stage_bytes < need) {
+        if (h->h_stage) {
+            cudaStreamSynchronize(h->stream);
+            cudaFree(h->h_stage);
+            h->h_stage = nullptr;
+            h->h_stage_bytes = 0;
+        }
+        if (cudaMalloc(&h->h_stage, need) != cudaSuccess) {
+            cudaGetLastError();
+            return SEV_ERR_WORKSPACE;
+        }
+        h->h_stage_bytes = need;
+    }
+    void *dA = h->h_stage;
+    double *dE = (double *)((char *)h->h_stage + abytes);
+    SEV_CUDA(cudaMemcpy2DAsync(dA, es * n, A_host, es * lda, es * n, n, cudaMemcpyHostToDevice, h->stream));
+    int rc = sev_eigvalsh(h, n, dA, n, b0, prec, dE);
+    if (rc) return rc;
+    SEV_CUDA(cudaMemcpyAsync(eigs_host, dE, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    return sev_get_error(h);
+}
+
+int sev_full_to_band(sev_handle h, int n, void *A, int lda, int b, int prec, void *AB, int ldab) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && !A) return -3;
+    if (lda < (n > 1 ? n : 1)) return -4;
+    if (b < 1) return -5;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -6;
+    if (n > 0 && !AB) return -7;
+    if (ldab < b + 1) return -8;
+    if (n == 0) return SEV_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    if (b >= n - 1) {
+        return prec == SEV_FP64 ? launch_band_from_dense<double>(h, n, (double *)A, lda, b, (double *)AB, ldab)
+                                : launch_band_from_dense<float>(h, n, (float *)A, lda, b, (float *)AB, ldab);
+    }
+    const size_t need = prec == SEV_FP64 ? full_to_band_workspace<double>(h, n, b) : full_to_band_workspace<float>(h, n, b);
+    void *ws = nullptr;
+    int rc = get_workspace(h, need, &ws);
+    if (rc) return rc;
+    return prec == SEV_FP64 ? launch_full_to_band<double>(h, n, (double *)A, lda, b, (double *)AB, ldab, ws, need)
+                            : launch_full_to_band<float>(h, n, (float *)A, lda, b, (float *)AB, ldab, ws, need);
+}
+
+int sev_band_to_band(sev_handle h, int n, void *AB, int ldab, int b, int hh, int prec) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && !AB) return -3;
+    if (ldab < 2 * b) return -4;
+    if (b < 2) return -5;
+    if (hh < 1 || hh >= b || b % hh != 0) return -6;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -7;
+    if (n == 0) return SEV_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    if ((prec == SEV_FP64 ? band_smem_bytes<double>(b, hh) : band_smem_bytes<float>(b, hh)) > h->smem_optin)
+        return SEV_ERR_UNSUPPORTED;
+    const size_t need = band_workspace(n, b, hh);
+    void *ws = nullptr;
+    int rc = get_workspace(h, need, &ws);
+    if (rc) return rc;
+    return prec == SEV_FP64 ? launch_band_to_band<double>(h, n, (double *)AB, ldab, b, hh, ws, need)
+                            : launch_band_to_band<float>(h, n, (float *)AB, ldab, b, hh, ws, need);
+}
+
+int sev_tridiag_bisect(sev_handle h, int n, const double *d, const double *e, double rtol, double *eigs) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && !d) return -3;
+    if (n > 1 && !e) return -4;
+    if (!(rtol > 0.0) || !(rtol < 1.0)) return -5;
+    if (n > 0 && !eigs) return -6;
+    if (n == 0) return SEV_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    const size_t need = bisect_workspace(n);
+    void *ws = nullptr;
+    int rc = get_workspace(h, need, &ws);
+    if (rc) return rc;
+    return launch_bisect(h, n, d, n > 1 ? e : d, rtol, eigs, ws, need);
+}
+
+int sev_band_tridiag_extract(sev_handle h, int n, const void *AB, int ldab, int prec, double *d, double *e) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (n > 0 && !AB) return -3;
+    if (ldab < 2) return -4;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -5;
+    if (n > 0 && !d) return -6;
+    if (n > 1 && !e) return -7;
+    if (n == 0) return SEV_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    return prec == SEV_FP64 ? launch_tridiag_extract<double>(h, n, (const double *)AB, ldab, d, e ? e : d)
+                            : launch_tridiag_extract<float>(h, n, (const float *)AB, ldab, d, e ? e : d);
+}
+
+int sev_get_error(sev_handle h) {
+    if (!h) return -1;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SEV_ERR_CUDA;
+    int v = 0;
+    if (cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SEV_ERR_CUDA;
+    if (v) cudaMemset(h->d_err, 0, sizeof(int));
+    return v;
+}
+
+const char *sev_status_string(int code) {
+    if (code < 0) return "invalid argument";
+    switch (code) {
+        case SEV_OK: return "ok";
+        case SEV_ERR_NONFINITE: return "input holds NaN or Inf";
+        case SEV_ERR_NOCONV: return "bisection did not converge within its iteration cap";
+        case SEV_ERR_TIMEOUT: return "a device-side wait hit its iteration cap";
+        case SEV_ERR_CUDA: return "CUDA runtime error";
+        case SEV_ERR_WORKSPACE: return "workspace too small or allocation failed";
+        case SEV_ERR_UNSUPPORTED: return "unsupported parameter combination";
+        case SEV_ERR_INTERNAL: return "internal index check failed";
+        default: return "unknown status";
+    }
+}
+
+int sev_set_kernel_timing(sev_handle h, unsigned long long mask) {
+    if (!h) return -1;
+    h->timing = mask;
+    return SEV_OK;
+}
+
+int sev_kernel_count(void) { return K_COUNT; }
+
+const char *sev_kernel_name(int k) { return (k >= 0 && k < K_COUNT) ? kKernelNames[k] : ""; }
+
+int sev_kernel_time(sev_handle h, int k, double *total_ms, long *launches, int reset) {
+    if (!h) return -1;
+    if (k < 0 || k >= K_COUNT) return -2;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SEV_ERR_CUDA;
+    drain_timing(h);
+    if (total_ms) *total_ms = h->tot_ms[k];
+    if (launches) *launches = h->launches[k];
+    if (reset) {
+        h->tot_ms[k] = 0.0;
+        h->launches[k] = 0;
+    }
+    return SEV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// band.cu -- band-to-band reduction b -> h (Algorithm 4.2) on packed lower
+// band storage, as one persistent kernel per stage.
+//
+// Chase (i, j) (1-based, as in the algorithm): with h the target width,
+//   o_qr.r = (i-1)h + (j-1)b + h
+//   j = 1: o_qr.c = o_qr.r - h, o_v = 0,     o_up.c = o_qr.r,      n_c = min(n - o_up.c, 2b)
+//   j > 1: o_qr.c = o_qr.r - b, o_v = b - h, o_up.c = o_qr.c + h,  n_c = min(n - o_up.c, 3b - h)
+//   n_r = min(n - o_qr.r, b); the chase exists while n - o_qr.r >= 2
+// and performs: QR of B[qr rows, qr cols] (n_r x h); write [R; 0];
+// W = B[up cols, qr rows] U T; V = -W; V[v rows] += 1/2 U (T^T (U^T W[v rows]));
+// B[qr rows, up cols] += U V^T and the mirrored B[up cols, qr rows] += V U^T.
+// With lower storage the mirrored pair is one entry: rows of W outside the
+// qr rows get X <- X - (X U T) U^T (one-sided), the qr-row block gets the
+// symmetric rank-2 update U V^T + V U^T.
+//
+// Schedule.  A CTA takes sweeps i in increasing order (global counter) and
+// runs its chases j = 1, 2, ...; chase (i, j) waits until sweep i-1 has
+// completed chase j+2 (or all of its chases).  Chase (i, j) overlaps chase
+// (i-1, j+2) -- its bulge rows [o+2b-h, o+2b) are the rows that (i-1, j+2)
+// factorises -- so the pipeline t = 2i + j that the Fig. 2 caption pictures
+// is not legal; this rule gives t = 3i + j and reproduces the sequential
+// order bit for bit.  Sweeps are handed out in order and each CTA finishes
+// its sweep before taking another, so every awaited sweep is held by a
+// running CTA: the waits cannot deadlock.  Every wait is capped; on expiry
+// the kernel latches SEV_ERR_TIMEOUT and returns.
+#include "common.cuh"
+
+namespace sev {
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__host__ __device__ __forceinline__ int band_num_chases(int n, int b, int h, int i) {
+    const int r = n - i * h;
+    return r < 2 ? 0 : (n - 2 - i * h) / b + 1;
+}
+__host__ __device__ __forceinline__ int band_num_sweeps(int n, int h) { return n >= 2 ? (n - 2) / h : 0; }
+
+// Band element (r, c) with r >= c; out-of-range indices are a bug: they are
+// not dereferenced, the CTA's flag is set and 0 is returned.
+template <typename T>
+__device__ __forceinline__ T bld(const T *AB, int ldab, int n, int r, int c, int *bad) {
+    const int d = r - c;
+    if (d < 0 || d >= ldab || r >= n || c < 0) {
+        *bad = 1;
+        return T(0);
+    }
+    return __ldcg(AB + d + (size_t)c * ldab);
+}
+template <typename T>
+__device__ __forceinline__ T bld_sym(const T *AB, int ldab, int n, int u, int q, int *bad) {
+    return u >= q ? bld(AB, ldab, n, u, q, bad) : bld(AB, ldab, n, q, u, bad);
+}
+template <typename T>
+__device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, int *bad) {
+    const int d = r - c;
+    if (d < 0 || d >= ldab || r >= n || c < 0) {
+        *bad = 1;
+        return;
+    }
+    AB[d + (size_t)c * ldab] = v;
+}
+template <typename T>
+__device__ __forceinline__ void bst_sym(T *AB, int ldab, int n, int u, int q, T v, int *bad) {
+    if (u >= q)
+        bst(AB, ldab, n, u, q, v, bad);
+    else
+        bst(AB, ldab, n, q, u, v, bad);
+}
+
+template <typename T>
+struct ChaseSmem {
+    T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau;
+    double *red;
+    int ldb1, ldh1;
+    __device__ ChaseSmem(unsigned char *base, int b, int h) {
+        ldb1 = b + 1;
+        ldh1 = h + 1;
+        Us = (T *)base;
+        UTs = Us + (size_t)ldb1 * h;
+        Xs = UTs + (size_t)ldb1 * h;
+        Ws = Xs + (size_t)ldb1 * b;
+        Ts = Ws + (size_t)ldb1 * h;
+        Zs = Ts + (size_t)ldh1 * h;
+        tau = Zs + (size_t)ldh1 * h;
+        size_t off = (size_t)((unsigned char *)(tau + h) - base);
+        off = (off + 15) & ~(size_t)15;
+        red = (double *)(base + off);
+    }
+};
+
+template <typename T>
+size_t band_smem_bytes(int b, int h) {
+    const size_t ldb1 = b + 1, ldh1 = h + 1;
+    size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h;
+    size_t bytes = e * sizeof(T);
+    bytes = (bytes + 15) & ~(size_t)15;
+    return bytes + 32 * sizeof(double);
+}
+
+// One chase (i, j) performed by the whole CTA.
+template <typename T>
+__device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, ChaseSmem<T> &S, int *bad) {
+    const int o_qr_r = (i - 1) * h + (j - 1) * b + h;
+    int o_qr_c, o_v, o_up_c, lim;
+    if (j == 1) {
+        o_qr_c = o_qr_r - h;
+        o_v = 0;
+        o_up_c = o_qr_r;
+        lim = 2 * b;
+    } else {
+        o_qr_c = o_qr_r - b;
+        o_v = b - h;
+        o_up_c = o_qr_c + h;
+        lim = 3 * b - h;
+    }
+    const int n_r = min(n - o_qr_r, b);
+    const int n_c = min(n - o_up_c, lim);
+    const int ldb1 = S.ldb1, ldh1 = S.ldh1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // 1. QR of the n_r x h block
+    for (int idx = tid; idx < n_r * h; idx += nt) {
+        const int r = idx % n_r, c = idx / n_r;
+        S.Xs[r + (size_t)c * ldb1] = bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad);
+    }
+    __syncthreads();
+    const int nr = cta_qr(n_r, h, S.Xs, ldb1, S.tau, S.red);
+    // 2. B[qr rows, qr cols] = [R; 0]
+    for (int idx = tid; idx < n_r * h; idx += nt) {
+        const int r = idx % n_r, c = idx / n_r;
+        const T v = (r <= c) ? S.Xs[r + (size_t)c * ldb1] : T(0);
+        bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, v, bad);
+    }
+    if (nr == 0) {
+        __syncthreads();
+        return;
+    }
+    // 3. U, T and U T
+    cta_extract_u(n_r, nr, nr, S.Xs, ldb1, S.Us, ldb1);
+    cta_form_t(n_r, nr, S.Xs, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
+    cta_gemm<T, false, false>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, T(0), S.UTs, ldb1);
+    __syncthreads();
+    // 4. the qr-row diagonal block X_d (n_r x n_r): two-sided update
+    for (int idx = tid; idx < n_r * n_r; idx += nt) {
+        const int r = idx % n_r, c = idx / n_r;
+        S.Xs[r + (size_t)c * ldb1] = bld_sym(AB, ldab, n, o_qr_r + r, o_qr_r + c, bad);
+    }
+    __syncthreads();
+    // W_d = X_d (U T)
+    cta_gemm<T, false, false>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
+    __syncthreads();
+    // S = U^T W_d
+    cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Ws, ldb1, T(0), S.Zs, ldh1);
+    __syncthreads();
+    // Z = T^T S, in place column by column (rows descending)
+    for (int c = tid; c < nr; c += nt) {
+        for (int a = nr - 1; a >= 0; --a) {
+            T s = 0;
+            for (int q = 0; q <= a; ++q) s += S.Ts[q + (size_t)a * ldh1] * S.Zs[q + (size_t)c * ldh1];
+            S.Zs[a + (size_t)c * ldh1] = s;
+        }
+    }
+    __syncthreads();
+    // V_d = -W_d + 1/2 U Z  (into Ws)
+    cta_gemm<T, false, false>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, T(-1), S.Ws, ldb1);
+    __syncthreads();
+    // X_d += U V_d^T + V_d U^T (lower half stored)
+    for (int idx = tid; idx < n_r * n_r; idx += nt) {
+        const int r = idx % n_r, c = idx / n_r;
+        if (r < c) continue;
+        T s = 0;
+        for (int m = 0; m < nr; ++m)
+            s += S.Us[r + (size_t)m * ldb1] * S.Ws[c + (size_t)m * ldb1] +
+                 S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
+        bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
+    }
+    __syncthreads();
+    // 5. the other rows of W (above: [0, o_v), below: [o_v + n_r, n_c)):
+    //    X <- X - (X U T) U^T, in chunks of at most b rows
+    for (int part = 0; part < 2; ++part) {
+        const int a_begin = part == 0 ? 0 : o_v + n_r;
+        const int a_end = part == 0 ? o_v : n_c;
+        for (int a0 = a_begin; a0 < a_end; a0 += b) {
+            const int rows = min(b, a_end - a0);
+            for (int idx = tid; idx < rows * n_r; idx += nt) {
+                const int r = idx % rows, c = idx / rows;
+                S.Xs[r + (size_t)c * ldb1] = bld_sym(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, bad);
+            }
+            __syncthreads();
+            cta_gemm<T, false, false>(rows, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
+            __syncthreads();
+            for (int idx = tid; idx < rows * n_r; idx += nt) {
+                const int r = idx % rows, c = idx / rows;
+                T s = 0;
+                for (int m = 0; m < nr; ++m) s += S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
+                bst_sym(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] - s, bad);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int ldab, int b, int h, int nsweeps,
+                                                               int *progress, int *sweep_ctr, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ChaseSmem<T> S(smem, b, h);
+    __shared__ int s_sweep, s_abort, s_bad;
+    if (threadIdx.x == 0) s_bad = 0;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s_sweep = atomicAdd(sweep_ctr, 1);
+            s_abort = 0;
+        }
+        __syncthreads();
+        const int s = s_sweep;
+        if (s >= nsweeps) break;
+        const int i = s + 1;
+        const int J = band_num_chases(n, b, h, i);
+        const int Jprev = i > 1 ? band_num_chases(n, b, h, i - 1) : 0;
+        for (int j = 1; j <= J; ++j) {
+            if (i > 1) {
+                if (threadIdx.x == 0) {
+                    const int need = min(j + 2, Jprev);
+                    long it = 0;
+                    while (ld_acquire(&progress[s - 1]) < need) {
+                        if (*(volatile int *)err != 0) {
+                            s_abort = 1;
+                            break;
+                        }
+                        if (++it > kSpinCap / 8) {
+                            latch_error(err, SEV_ERR_TIMEOUT);
+                            s_abort = 1;
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+                }
+                __syncthreads();
+                if (s_abort) return;
+            }
+            band_chase(AB, ldab, n, b, h, i, j, S, &s_bad);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                st_release(&progress[s], j);
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_bad) latch_error(err, SEV_ERR_INTERNAL);
+}
+
+size_t band_workspace(int n, int b, int h) {
+    Carver c(nullptr);
+    c.take<int>((size_t)band_num_sweeps(n, h) + 1);
+    c.take<int>(1);
+    return c.bytes();
+}
+
+template <typename T>
+int launch_band_to_band(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, void *ws, size_t ws_bytes) {
+    const int nsweeps = band_num_sweeps(n, h);
+    if (nsweeps <= 0) return SEV_OK;
+    if (ws_bytes < band_workspace(n, b, h)) return SEV_ERR_WORKSPACE;
+    const size_t smem = band_smem_bytes<T>(b, h);
+    if (smem > hd->smem_optin) return SEV_ERR_UNSUPPORTED;
+    Carver c(ws);
+    int *progress = c.take<int>((size_t)nsweeps + 1);
+    int *ctr = c.take<int>(1);
+    SEV_CUDA(cudaMemsetAsync(progress, 0, sizeof(int) * ((size_t)nsweeps + 1), hd->stream));
+    SEV_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), hd->stream));
+    SEV_CUDA(cudaFuncSetAttribute(band_chase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_chase_kernel<T>, kThreads, smem));
+    if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
+    int grid = hd->sm_count * per_sm;
+    if (grid > nsweeps) grid = nsweeps;
+    SEV_LAUNCH(hd, K_BAND_CHASE, band_chase_kernel<T>, grid, kThreads, smem, n, AB, ldab, b, h, nsweeps, progress,
+               ctr, hd->d_err);
+    return SEV_OK;
+}
+
+template int launch_band_to_band<float>(sev_ctx *, int, float *, int, int, int, void *, size_t);
+template int launch_band_to_band<double>(sev_ctx *, int, double *, int, int, int, void *, size_t);
+template size_t band_smem_bytes<float>(int, int);
+template size_t band_smem_bytes<double>(int, int);
+
+}  // namespace sev

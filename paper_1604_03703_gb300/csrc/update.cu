@@ -1,0 +1,350 @@
+// update.cu -- the two-sided trailing update of the full-to-band reduction
+// (Eq. 4.1 as used in Algorithm 4.1) and the full-to-band driver.
+//
+// Per panel, with U (N x b) and T (b x b) from panel.cu and A22 the lower-
+// stored trailing matrix:
+//   Y  = A22 U                       (symm: reads A22 symmetrically)
+//   X  = Y T                         (= W T in the algorithm's notation)
+//   Zm = T^T (U^T X)
+//   V  = 1/2 U Zm - X                (the V_1 line of Algorithm 4.1)
+//   A22 <- A22 + U V^T + V U^T       (syr2k, lower tiles only)
+//
+// These SIMT kernels (64 x 64 output tiles, 4 x 4 per thread, FMA on the
+// CUDA cores) run the FP64 form at the FP64 pipe's rate; the mixed form's
+// symm and syr2k use the tensor-core kernels of update_tc.cu.
+#include "common.cuh"
+
+namespace sev {
+
+template <typename T>
+int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws);
+template <typename T>
+size_t panel_workspace(sev_ctx *h, int n, int b);
+template <typename T>
+int tc_update_supported(sev_ctx *h, int N, int b);
+template <typename T>
+int tc_symm(sev_ctx *h, int N, int b, const T *A22, int lda, const T *U, T *Y, void *ws);
+template <typename T>
+int tc_syr2k(sev_ctx *h, int N, int b, T *A22, int lda, const T *U, const T *V, void *ws);
+template <typename T>
+size_t tc_workspace(int n, int b);
+
+constexpr int BM = 64, BN = 64, BK = 16, PADT = 4;
+
+template <typename T>
+struct Tile {
+    T As[BK][BM + PADT];
+    T Bs[BK][BN + PADT];
+};
+
+template <typename T>
+__device__ __forceinline__ void tile_mma(const Tile<T> &t, T (&acc)[4][4]) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+        T a[4], bb[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] = t.As[k][tx + 16 * i];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) bb[j] = t.Bs[k][ty + 16 * j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+    }
+}
+
+// A slab (BM x BK) where element (m, k) = src[m + k*ld] (m contiguous).
+template <typename T>
+__device__ __forceinline__ void load_a_mcont(Tile<T> &t, const T *src, int ld, int m0, int k0, int M, int K) {
+    for (int idx = threadIdx.x; idx < BM * BK; idx += blockDim.x) {
+        const int m = idx % BM, k = idx / BM;
+        const int gm = m0 + m, gk = k0 + k;
+        t.As[k][m] = (gm < M && gk < K) ? src[(size_t)gm + (size_t)gk * ld] : T(0);
+    }
+}
+// A slab where element (m, k) = src[k + m*ld] (k contiguous).
+template <typename T>
+__device__ __forceinline__ void load_a_kcont(Tile<T> &t, const T *src, int ld, int m0, int k0, int M, int K) {
+    for (int idx = threadIdx.x; idx < BM * BK; idx += blockDim.x) {
+        const int k = idx % BK, m = idx / BK;
+        const int gm = m0 + m, gk = k0 + k;
+        t.As[k][m] = (gm < M && gk < K) ? src[(size_t)gk + (size_t)gm * ld] : T(0);
+    }
+}
+// B slab (BK x BN) where element (k, n) = src[k + n*ld] (k contiguous).
+template <typename T>
+__device__ __forceinline__ void load_b_kcont(Tile<T> &t, const T *src, int ld, int k0, int n0, int K, int N) {
+    for (int idx = threadIdx.x; idx < BK * BN; idx += blockDim.x) {
+        const int k = idx % BK, n = idx / BK;
+        const int gk = k0 + k, gn = n0 + n;
+        t.Bs[k][n] = (gk < K && gn < N) ? src[(size_t)gk + (size_t)gn * ld] : T(0);
+    }
+}
+// B slab where element (k, n) = src[n + k*ld] (n contiguous).
+template <typename T>
+__device__ __forceinline__ void load_b_ncont(Tile<T> &t, const T *src, int ld, int k0, int n0, int K, int N) {
+    for (int idx = threadIdx.x; idx < BK * BN; idx += blockDim.x) {
+        const int n = idx % BN, k = idx / BN;
+        const int gk = k0 + k, gn = n0 + n;
+        t.Bs[k][n] = (gk < K && gn < N) ? src[(size_t)gn + (size_t)gk * ld] : T(0);
+    }
+}
+
+// Y = A22 U, A22 symmetric N x N stored in its lower triangle.
+template <typename T>
+__global__ void __launch_bounds__(256) symm_kernel(int N, int b, const T *__restrict__ A, int lda,
+                                                   const T *__restrict__ U, int ldu, T *__restrict__ Y, int ldy) {
+    __shared__ Tile<T> t;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    T acc[4][4] = {};
+    for (int k0 = 0; k0 < N; k0 += BK) {
+        if (k0 + BK <= m0) {
+            load_a_mcont(t, A, lda, m0, k0, N, N);  // strictly below the diagonal
+        } else if (k0 >= m0 + BM) {
+            load_a_kcont(t, A, lda, m0, k0, N, N);  // strictly above: A(m,k) = A(k,m)
+        } else {
+            for (int idx = threadIdx.x; idx < BM * BK; idx += blockDim.x) {
+                const int m = idx % BM, k = idx / BM;
+                const int gm = m0 + m, gk = k0 + k;
+                T v = 0;
+                if (gm < N && gk < N) v = gm >= gk ? A[(size_t)gm + (size_t)gk * lda] : A[(size_t)gk + (size_t)gm * lda];
+                t.As[k][m] = v;
+            }
+        }
+        load_b_kcont(t, U, ldu, k0, n0, N, b);
+        __syncthreads();
+        tile_mma(t, acc);
+        __syncthreads();
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+            if (m < N && n < b) Y[(size_t)m + (size_t)n * ldy] = acc[i][j];
+        }
+}
+
+// C = alpha * A B + beta * D, A (M x K, m contiguous), B (K x Nc, k contiguous, ld ldb).
+// Used for X = Y T and V = 1/2 U Zm - X.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_nn_kernel(int M, int Nc, int K, T alpha, const T *__restrict__ A, int lda,
+                                                      const T *__restrict__ B, int ldb, T beta,
+                                                      const T *__restrict__ D, int ldd, T *__restrict__ C, int ldc) {
+    __shared__ Tile<T> t;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    T acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        load_a_mcont(t, A, lda, m0, k0, M, K);
+        load_b_kcont(t, B, ldb, k0, n0, K, Nc);
+        __syncthreads();
+        tile_mma(t, acc);
+        __syncthreads();
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+            if (m < M && n < Nc) {
+                T v = alpha * acc[i][j];
+                if (beta != T(0)) v += beta * D[(size_t)m + (size_t)n * ldd];
+                C[(size_t)m + (size_t)n * ldc] = v;
+            }
+        }
+}
+
+// Partial products P_s = U[rows_s]^T X[rows_s] (b x b) for row chunk s.
+template <typename T>
+__global__ void __launch_bounds__(256) utx_partial_kernel(int N, int b, int chunk, const T *__restrict__ U, int ldu,
+                                                          const T *__restrict__ X, int ldx, T *__restrict__ part) {
+    __shared__ Tile<T> t;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, s = blockIdx.z;
+    const int kbeg = s * chunk, kend = min(N, kbeg + chunk);
+    T acc[4][4] = {};
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        // A(m = a, k = i) = U[i, a] (k contiguous); B(k = i, n = c) = X[i, c]
+        for (int idx = threadIdx.x; idx < BM * BK; idx += blockDim.x) {
+            const int k = idx % BK, m = idx / BK;
+            const int gm = m0 + m, gk = k0 + k;
+            t.As[k][m] = (gm < b && gk < kend) ? U[(size_t)gk + (size_t)gm * ldu] : T(0);
+        }
+        for (int idx = threadIdx.x; idx < BK * BN; idx += blockDim.x) {
+            const int k = idx % BK, n = idx / BK;
+            const int gk = k0 + k, gn = n0 + n;
+            t.Bs[k][n] = (gk < kend && gn < b) ? X[(size_t)gk + (size_t)gn * ldx] : T(0);
+        }
+        __syncthreads();
+        tile_mma(t, acc);
+        __syncthreads();
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    T *P = part + (size_t)s * b * b;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+            if (m < b && n < b) P[m + (size_t)n * b] = acc[i][j];
+        }
+}
+
+// Zm = T^T (sum_s P_s): CTA handles 16 columns; sums the partials in a fixed
+// order (deterministic), then applies T^T.
+template <typename T>
+__global__ void __launch_bounds__(256) utx_reduce_kernel(int b, int nparts, const T *__restrict__ part,
+                                                         const T *__restrict__ Tm, T *__restrict__ Zm) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *Ms = (T *)smem;  // b x 16
+    const int c0 = blockIdx.x * 16;
+    const int nc = min(16, b - c0);
+    for (int idx = threadIdx.x; idx < b * nc; idx += blockDim.x) {
+        const int a = idx % b, c = idx / b;
+        T s = 0;
+        for (int p = 0; p < nparts; ++p) s += part[(size_t)p * b * b + a + (size_t)(c0 + c) * b];
+        Ms[a + (size_t)c * b] = s;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < b * nc; idx += blockDim.x) {
+        const int a = idx % b, c = idx / b;
+        T s = 0;
+        for (int q = 0; q <= a; ++q) s += Tm[q + (size_t)a * b] * Ms[q + (size_t)c * b];
+        Zm[a + (size_t)(c0 + c) * b] = s;
+    }
+}
+
+// A22 += U V^T + V U^T on the lower tiles (tile (I, J), I >= J).
+template <typename T>
+__global__ void __launch_bounds__(256) syr2k_kernel(int N, int b, T *__restrict__ A, int lda, const T *__restrict__ U,
+                                                    int ldu, const T *__restrict__ V, int ldv) {
+    __shared__ Tile<T> t;
+    const long x = blockIdx.x;
+    int I = (int)((sqrt(8.0 * (double)x + 1.0) - 1.0) * 0.5);
+    while ((long)(I + 1) * (I + 2) / 2 <= x) ++I;
+    while ((long)I * (I + 1) / 2 > x) --I;
+    const int J = (int)(x - (long)I * (I + 1) / 2);
+    const int m0 = I * BM, n0 = J * BN;
+    T acc[4][4] = {};
+    const int K2 = 2 * b;
+    for (int k0 = 0; k0 < K2; k0 += BK) {
+        for (int idx = threadIdx.x; idx < BM * BK; idx += blockDim.x) {
+            const int m = idx % BM, k = idx / BM;
+            const int gm = m0 + m, gk = k0 + k;
+            T v = 0;
+            if (gm < N && gk < K2) v = gk < b ? U[(size_t)gm + (size_t)gk * ldu] : V[(size_t)gm + (size_t)(gk - b) * ldv];
+            t.As[k][m] = v;
+        }
+        for (int idx = threadIdx.x; idx < BK * BN; idx += blockDim.x) {
+            const int n = idx % BN, k = idx / BN;
+            const int gk = k0 + k, gn = n0 + n;
+            T v = 0;
+            if (gn < N && gk < K2) v = gk < b ? V[(size_t)gn + (size_t)gk * ldv] : U[(size_t)gn + (size_t)(gk - b) * ldu];
+            t.Bs[k][n] = v;
+        }
+        __syncthreads();
+        tile_mma(t, acc);
+        __syncthreads();
+    }
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int m = m0 + tx + 16 * i, n = n0 + ty + 16 * j;
+            if (m < N && n < N && m >= n) A[(size_t)m + (size_t)n * lda] += acc[i][j];
+        }
+}
+
+// --------------------------------------------------------------- driver
+template <typename T>
+struct F2BBuffers {
+    T *U, *Y, *X, *V, *Tm, *Zm, *part;
+    void *panel_ws, *tc_ws;
+};
+
+static int utx_parts(int N) {
+    int p = (N + 1023) / 1024;
+    return p < 1 ? 1 : (p > 64 ? 64 : p);
+}
+
+template <typename T>
+static void carve_f2b(Carver &c, F2BBuffers<T> &B, sev_ctx *h, int n, int b, bool tc) {
+    B.U = c.take<T>((size_t)n * b);
+    B.Y = c.take<T>((size_t)n * b);
+    B.X = c.take<T>((size_t)n * b);
+    B.V = c.take<T>((size_t)n * b);
+    B.Tm = c.take<T>((size_t)b * b);
+    B.Zm = c.take<T>((size_t)b * b);
+    B.part = c.take<T>((size_t)utx_parts(n) * b * b);
+    B.tc_ws = tc ? (void *)c.take<char>(tc_workspace<T>(n, b)) : nullptr;
+    B.panel_ws = c.take<char>(panel_workspace<T>(h, n, b));
+}
+
+template <typename T>
+size_t full_to_band_workspace(sev_ctx *h, int n, int b) {
+    Carver c(nullptr);
+    F2BBuffers<T> B;
+    carve_f2b<T>(c, B, h, n, b, true);
+    return c.bytes();
+}
+
+template <typename T>
+int launch_full_to_band(sev_ctx *h, int n, T *A, int lda, int b, T *AB, int ldab, void *ws, size_t ws_bytes) {
+    if (n <= 0) return SEV_OK;
+    if (ws_bytes < full_to_band_workspace<T>(h, n, b)) return SEV_ERR_WORKSPACE;
+    Carver c(ws);
+    F2BBuffers<T> B;
+    carve_f2b<T>(c, B, h, n, b, true);
+    for (int k = 0;; ++k) {
+        const int c0 = k * b, r0 = c0 + b;
+        if (r0 >= n) break;
+        const int N = n - r0;
+        if (N < 2) break;
+        T *P = A + (size_t)r0 + (size_t)c0 * lda;
+        T *A22 = A + (size_t)r0 + (size_t)r0 * lda;
+        int rc = panel_factor<T>(h, N, b, P, lda, B.U, B.Tm, B.panel_ws);
+        if (rc) return rc;
+        const bool tc = tc_update_supported<T>(h, N, b);
+        // Y = A22 U
+        if (tc) {
+            rc = tc_symm<T>(h, N, b, A22, lda, B.U, B.Y, B.tc_ws);
+            if (rc) return rc;
+        } else {
+            SEV_LAUNCH(h, K_SYMM, symm_kernel<T>, dim3((N + BM - 1) / BM, (b + BN - 1) / BN), 256, 0, N, b, A22, lda,
+                       B.U, N, B.Y, N);
+        }
+        // X = Y T
+        SEV_LAUNCH(h, K_VFORM_XT, gemm_nn_kernel<T>, dim3((N + BM - 1) / BM, (b + BN - 1) / BN), 256, 0, N, b, b, T(1),
+                   B.Y, N, B.Tm, b, T(0), (const T *)nullptr, N, B.X, N);
+        // Zm = T^T (U^T X)
+        const int parts = utx_parts(N);
+        const int chunk = (((N + parts - 1) / parts) + BK - 1) / BK * BK;
+        SEV_LAUNCH(h, K_VFORM_UTX, utx_partial_kernel<T>, dim3((b + BM - 1) / BM, (b + BN - 1) / BN, parts), 256, 0, N,
+                   b, chunk, B.U, N, B.X, N, B.part);
+        SEV_LAUNCH(h, K_VFORM_REDUCE, utx_reduce_kernel<T>, (b + 15) / 16, 256, sizeof(T) * (size_t)b * 16, b, parts,
+                   B.part, B.Tm, B.Zm);
+        // V = 1/2 U Zm - X
+        SEV_LAUNCH(h, K_VFORM_V, gemm_nn_kernel<T>, dim3((N + BM - 1) / BM, (b + BN - 1) / BN), 256, 0, N, b, b,
+                   T(0.5), B.U, N, B.Zm, b, T(-1), B.X, N, B.V, N);
+        // A22 += U V^T + V U^T
+        if (tc) {
+            rc = tc_syr2k<T>(h, N, b, A22, lda, B.U, B.V, B.tc_ws);
+            if (rc) return rc;
+        } else {
+            const long nt = (N + BM - 1) / BM;
+            SEV_LAUNCH(h, K_SYR2K, syr2k_kernel<T>, (unsigned)(nt * (nt + 1) / 2), 256, 0, N, b, A22, lda, B.U, N, B.V,
+                       N);
+        }
+    }
+    return launch_band_from_dense<T>(h, n, A, lda, b, AB, ldab);
+}
+
+template int launch_full_to_band<float>(sev_ctx *, int, float *, int, int, float *, int, void *, size_t);
+template int launch_full_to_band<double>(sev_ctx *, int, double *, int, int, double *, int, void *, size_t);
+template size_t full_to_band_workspace<float>(sev_ctx *, int, int);
+template size_t full_to_band_workspace<double>(sev_ctx *, int, int);
+
+}  // namespace sev

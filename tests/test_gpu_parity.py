@@ -1,0 +1,254 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Sizes span several tiles/leaves and ragged tails; FP64 tolerances follow
+from the arithmetic (backward-stable orthogonal similarities: c n u ||A||),
+the mixed form is held to its stated 1e-4 ||A||_2."""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1604_03703_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+EPS64 = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    return torch
+
+
+@pytest.fixture(scope="module")
+def H(torch_cuda):
+    from paper_1604_03703_gb300 import build as B
+
+    B.build()
+    from paper_1604_03703_gb300 import api
+
+    h = api.Handle(0)
+    yield h
+    h.close()
+
+
+def dev(torch, a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def to_band_tensor(torch, A, ldab, dtype):
+    return dev(torch, I.dense_to_band(A, ldab).T, dtype)
+
+
+def band_dense(AB_t):
+    AB = AB_t.double().cpu().numpy().T  # (ldab, n)
+    return I.band_to_dense(AB)
+
+
+# ----------------------------------------------------------------- bisection
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (3, 2), (37, 3), (1000, 4), (4099, 5)])
+def test_bisect_bitwise_vs_oracle(H, torch_cuda, orc, n, seed):
+    torch = torch_cuda
+    d, e = I.random_tridiagonal(n, 100 + seed)
+    got = H.tridiag_bisect(dev(torch, d), dev(torch, e), 1e-14).cpu().numpy()
+    H.raise_device_error()
+    ref = orc.bisect(d, e, 1e-14)
+    np.testing.assert_array_equal(got, ref)
+
+
+@pytest.mark.parametrize("rtol", [1e-6, 1e-9, 1e-14])
+def test_bisect_toeplitz_closed_form(H, torch_cuda, orc, rtol):
+    torch = torch_cuda
+    d, e, lam = I.toeplitz(777, 0.5, -1.25)
+    got = H.tridiag_bisect(dev(torch, d), dev(torch, e), rtol).cpu().numpy()
+    np.testing.assert_array_equal(got, orc.bisect(d, e, rtol))
+    assert np.abs(got - lam).max() <= (rtol + 4 * EPS64) * 3.0
+
+
+def test_bisect_clusters_and_zeros(H, torch_cuda, orc):
+    torch = torch_cuda
+    d = np.repeat(np.array([-1.0, 0.0, 2.0]), 50)
+    e = np.zeros(149)
+    e[::7] = 1e-12
+    got = H.tridiag_bisect(dev(torch, d), dev(torch, e), 1e-14).cpu().numpy()
+    np.testing.assert_array_equal(got, orc.bisect(d, e, 1e-14))
+
+
+# -------------------------------------------------------------- band-to-band
+BAND_CASES = [(200, 8, 4), (203, 16, 8), (150, 6, 3), (161, 32, 16), (97, 4, 1), (130, 8, 2), (64, 2, 1), (5, 2, 1),
+              (40, 32, 16)]
+
+
+@pytest.mark.parametrize("n,b,h", BAND_CASES)
+def test_band_to_band_fp64_vs_oracle(H, torch_cuda, orc, n, b, h):
+    torch = torch_cuda
+    A = I.random_band(n, b, 7000 + n + b + h)
+    AB = to_band_tensor(torch, A, 2 * b, torch.float64)
+    H.band_to_band(AB, b, h)
+    H.raise_device_error()
+    got = band_dense(AB)
+    ref = orc.band_to_band(A, b, h)
+    scale = np.linalg.norm(A)
+    # rounding grows with the number of similarities an entry goes through (~n/h)
+    np.testing.assert_allclose(np.tril(got), np.tril(ref), atol=20 * n * EPS64 * scale, rtol=0)
+    i, j = np.indices(got.shape)
+    assert np.all(got[np.abs(i - j) > h] == 0.0)
+
+
+@pytest.mark.parametrize("n,b,h", [(300, 16, 8), (257, 64, 32), (411, 128, 64), (200, 8, 4)])
+def test_band_to_band_fp32_vs_oracle(H, torch_cuda, orc, n, b, h):
+    torch = torch_cuda
+    A = I.random_band(n, b, 7100 + n + b)
+    AB = to_band_tensor(torch, A, 2 * b, torch.float32)
+    H.band_to_band(AB, b, h)
+    H.raise_device_error()
+    got = band_dense(AB)
+    ref = orc.band_to_band(A, b, h)
+    scale = np.linalg.norm(A)
+    assert np.abs(np.tril(got) - np.tril(ref)).max() <= 2e-5 * scale
+    lam = np.linalg.eigvalsh(A)
+    assert np.abs(np.linalg.eigvalsh(got) - lam).max() <= 1e-5 * np.abs(lam).max()
+
+
+# -------------------------------------------------------------- full-to-band
+F2B_CASES = [
+    # n, b, leaf rows override (0 = library default; small values force a deep tree)
+    (130, 8, 0),
+    (300, 16, 32),
+    (301, 16, 16),
+    (517, 32, 64),
+    (700, 32, 0),
+    (257, 64, 64),
+    (64, 8, 0),
+    (40, 32, 0),
+]
+
+
+@pytest.mark.parametrize("n,b,leaf", F2B_CASES)
+def test_full_to_band_fp64_vs_oracle(torch_cuda, orc, n, b, leaf, monkeypatch):
+    torch = torch_cuda
+    from paper_1604_03703_gb300 import api
+    from paper_1604_03703_gb300 import build as B
+
+    B.build()
+    if leaf:
+        monkeypatch.setenv("SEV_LEAF_ROWS", str(leaf))
+    h = api.Handle(0)  # reads SEV_LEAF_ROWS at creation
+    A = I.semicircle(n, 8000 + n + b)
+    At = dev(torch, A, torch.float64)
+    AB = h.full_to_band(At, b)
+    h.raise_device_error()
+    got = band_dense(AB)
+    ref = orc.full_to_band(A, b)
+    scale = np.linalg.norm(A)
+    # the band is unique up to the reflector signs, which both sides fix the
+    # same way (tau in [1, 2]); compare entries
+    np.testing.assert_allclose(np.tril(got), np.tril(ref), atol=20 * n * EPS64 * scale, rtol=0)
+    h.close()
+
+
+@pytest.mark.parametrize("n,b", [(600, 32), (333, 64), (1100, 128)])
+def test_full_to_band_fp32_vs_oracle(H, torch_cuda, orc, n, b):
+    torch = torch_cuda
+    A = I.semicircle(n, 8100 + n + b)
+    AB = H.full_to_band(dev(torch, A, torch.float32), b)
+    H.raise_device_error()
+    got = band_dense(AB)
+    ref = orc.full_to_band(A, b)
+    scale = np.linalg.norm(A)
+    assert np.abs(np.tril(got) - np.tril(ref)).max() <= 1e-4 * scale
+    lam = np.linalg.eigvalsh(A)
+    assert np.abs(np.linalg.eigvalsh(got) - lam).max() <= 1e-4 * np.abs(lam).max()
+
+
+# --------------------------------------------------------------- end to end
+def test_eigvalsh_qdq512_fp64(H, torch_cuda, orc):
+    """n = 512, A = Q diag(linspace(-1, 1)) Q^T, b0 = 32: halvings 32 -> ... -> 1."""
+    torch = torch_cuda
+    A, D = I.workload_qdq512()
+    ref = orc.eigvalsh(A, 1e-14)
+    got = H.eigvalsh(dev(torch, A, torch.float64), 32).cpu().numpy()
+    H.raise_device_error()
+    norm = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-11 * norm
+    assert np.abs(got - D).max() <= 1e-11 * norm
+
+
+def test_eigvalsh_qdq512_mixed(H, torch_cuda, orc):
+    torch = torch_cuda
+    A, D = I.workload_qdq512()
+    ref = orc.eigvalsh(A, 1e-14)
+    got = H.eigvalsh(dev(torch, A, torch.float32), 32).cpu().numpy()
+    H.raise_device_error()
+    assert np.abs(got - ref).max() <= 1e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n,b0", [(1, 4), (2, 4), (3, 1), (4, 2), (9, 8), (33, 6), (100, 1), (129, 16), (250, 3)])
+def test_eigvalsh_edge_sizes(H, torch_cuda, orc, n, b0):
+    torch = torch_cuda
+    A = I.semicircle(n, 9000 + n)
+    ref = orc.eigvalsh(A, 1e-14)
+    got = H.eigvalsh(dev(torch, A, torch.float64), b0).cpu().numpy()
+    H.raise_device_error()
+    assert np.abs(got - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1e-300)
+
+
+@pytest.mark.parametrize("kind", ["zero", "diagonal", "banded", "rank1"])
+def test_eigvalsh_degenerate_inputs(H, torch_cuda, orc, kind):
+    torch = torch_cuda
+    n = 150
+    if kind == "zero":
+        A = np.zeros((n, n))
+    elif kind == "diagonal":
+        A = np.diag(I.rng(3).standard_normal(n))
+    elif kind == "banded":
+        A = I.random_band(n, 3, 4)
+    else:
+        v = I.rng(5).standard_normal(n)
+        A = np.outer(v, v)
+    ref = orc.eigvalsh(A, 1e-14)
+    got = H.eigvalsh(dev(torch, A, torch.float64), 16).cpu().numpy()
+    H.raise_device_error()
+    assert np.abs(got - ref).max() <= 1e-11 * max(np.abs(ref).max(), 1.0)
+
+
+def test_eigvalsh_host_entry(H, torch_cuda, orc):
+    torch = torch_cuda
+    A = I.semicircle(300, 77)
+    ref = orc.eigvalsh(A, 1e-14)
+    got = H.eigvalsh_host(torch.from_numpy(A.copy()).pin_memory(), 32).numpy()
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_caller_workspace(H, torch_cuda, orc):
+    torch = torch_cuda
+    n, b0 = 200, 16
+    A = I.semicircle(n, 78)
+    need = H.workspace_query(n, b0, 0)
+    ws = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    H.set_workspace(ws)
+    try:
+        got = H.eigvalsh(dev(torch, A, torch.float64), b0).cpu().numpy()
+    finally:
+        H.set_workspace(None)
+    assert np.abs(got - orc.eigvalsh(A, 1e-14)).max() <= 1e-11 * np.abs(got).max()
+
+
+def test_argument_errors(H, torch_cuda):
+    torch = torch_cuda
+    from paper_1604_03703_gb300._lib import SevError
+
+    A = torch.zeros(8, 8, dtype=torch.float64, device="cuda")
+    with pytest.raises(SevError) as ei:
+        H.band_to_band(torch.zeros(8, 3, dtype=torch.float64, device="cuda"), 2, 1)  # ldab < 2b
+    assert ei.value.code == -4
+    with pytest.raises(SevError) as ei:
+        H.band_to_band(torch.zeros(8, 8, dtype=torch.float64, device="cuda"), 4, 3)  # h does not divide b
+    assert ei.value.code == -6
+    with pytest.raises(SevError):
+        H.tridiag_bisect(A[0], A[0][:7], -1.0)

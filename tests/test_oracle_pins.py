@@ -322,3 +322,9 @@ def test_band_to_band_wavefront_legality(orc, n, b, h):
         np.testing.assert_array_equal(orc.band_to_band_wavefront(A, b, h, 3, tie), seq)
     two = [np.array_equal(orc.band_to_band_wavefront(A, b, h, 2, tie), seq) for tie in (False, True)]
     assert not all(two)
+
+
+def test_bisect_range_matches_full(orc):
+    d, e = I.random_tridiagonal(90, 12)
+    full = orc.bisect(d, e, 1e-14)
+    np.testing.assert_array_equal(orc.bisect_range(d, e, 10, 33, 1e-14), full[10:33])
