@@ -139,6 +139,28 @@ int sev_band_to_band(sev_handle handle, int n, void *AB, int ldab, int b, int h,
 int sev_tridiag_bisect(sev_handle handle, int n, const double *d, const double *e, double rtol,
                        double *eigs);
 
+/*
+ * Allocation-free bisection (no counterpart in the paper; a service for
+ * callers that cannot allocate device memory -- e.g. code that runs inside a
+ * framework owning every device allocation, or a latency-critical path that
+ * must not pay cudaMalloc's implicit device synchronisation).
+ * Same result as sev_tridiag_bisect, bit for bit, with no handle and no
+ * allocation: its scratch is a fixed device array inside the library of
+ * (65536 + 8) doubles (~512 KiB), resident on every device that loads the
+ * library until the process exits.
+ *   n       0 <= n <= 65536; larger n returns -1
+ *   d, e    device, n and n-1 doubles;  eigs: device, n doubles, ascending
+ *   rtol    1e-16 <= rtol < 1 (the bisection then always converges well
+ *           inside its iteration cap, so no device-side status is needed)
+ *   stream  cudaStream_t (as void*) on which the kernels are enqueued
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Every call on a device shares the one array, which keeps the last call's
+ * contents: calls whose kernels overlap on the GPU (different streams
+ * without ordering between them) race and must be serialised by the caller.
+ */
+int sev_tridiag_bisect_static(int n, const double *d, const double *e, double rtol, double *eigs, void *stream);
+
 /* Copy the diagonal and first subdiagonal of a packed band (float or double
  * by prec) into FP64 device arrays d (n) and e (n-1). */
 int sev_band_tridiag_extract(sev_handle handle, int n, const void *AB, int ldab, int prec, double *d,

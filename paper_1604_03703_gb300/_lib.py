@@ -40,6 +40,7 @@ SIGNATURES = {
     "sev_band_to_band": (_i, [_vp, _i, _vp, _i, _i, _i, _i]),
     "sev_tridiag_bisect": (_i, [_vp, _i, _vp, _vp, _d, _vp]),
     "sev_band_tridiag_extract": (_i, [_vp, _i, _vp, _i, _i, _vp, _vp]),
+    "sev_tridiag_bisect_static": (_i, [_i, _vp, _vp, _d, _vp, _vp]),
     "sev_get_error": (_i, [_vp]),
     "sev_status_string": (ctypes.c_char_p, [_i]),
     "sev_set_kernel_timing": (_i, [_vp, ctypes.c_ulonglong]),

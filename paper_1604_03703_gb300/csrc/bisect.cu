@@ -165,3 +165,56 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
 }
 
 }  // namespace sev
+
+// ------------------------------------------------- allocation-free variant
+// sev_tridiag_bisect_static: the same two kernels as sev_tridiag_bisect, but
+// their scratch (the squared off-diagonal, the Gershgorin/pivmin parameters
+// and an unused status slot) lives in this file-scope device array instead
+// of handle workspace, so a call allocates nothing.  The array is
+// (kStaticMaxN + 8) doubles (~512 KiB) on every device that loads the
+// library, held until the process exits.
+namespace sev {
+constexpr int kStaticMaxN = 65536;
+static __device__ __align__(256) double g_bisect_scratch[kStaticMaxN + 8];
+
+struct StaticScratch {
+    double *ptr = nullptr;
+    int sm_count = 0;
+};
+static StaticScratch g_static_dev[128];
+}  // namespace sev
+
+extern "C" int sev_tridiag_bisect_static(int n, const double *d, const double *e, double rtol, double *eigs,
+                                         void *stream) {
+    using namespace sev;
+    if (n < 0 || n > kStaticMaxN) return -1;
+    if (n > 0 && !d) return -2;
+    if (n > 1 && !e) return -3;
+    if (!(rtol >= 1e-16) || !(rtol < 1.0)) return -4;
+    if (n > 0 && !eigs) return -5;
+    if (n == 0) return SEV_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return SEV_ERR_CUDA;
+    StaticScratch &S = g_static_dev[dev];
+    if (!S.ptr) {
+        // once per device, with that device current: the array's device
+        // address (the host-side name is only a stand-in for it)
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bisect_scratch) != cudaSuccess) return SEV_ERR_CUDA;
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SEV_ERR_CUDA;
+        S.sm_count = sms;
+        S.ptr = (double *)p;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double *e2 = S.ptr;                   // n + 1 doubles
+    double *par = S.ptr + kStaticMaxN + 2;  // 4 doubles
+    int *status = (int *)(S.ptr + kStaticMaxN + 6);
+    if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SEV_ERR_CUDA;
+    bisect_prep_kernel<<<1, 1024, 0, st>>>(n, d, n > 1 ? e : d, e2, par);
+    if (cudaGetLastError() != cudaSuccess) return SEV_ERR_CUDA;
+    int bs = 64;
+    while (bs > 32 && (n + bs - 1) / bs < S.sm_count) bs >>= 1;
+    bisect_kernel<<<(n + bs - 1) / bs, bs, 0, st>>>(n, d, e2, par, rtol, 200, eigs, status);
+    return cudaGetLastError() == cudaSuccess ? SEV_OK : SEV_ERR_CUDA;
+}
