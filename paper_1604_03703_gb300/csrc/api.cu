@@ -11,7 +11,7 @@
 namespace sev {
 
 const char *const kKernelNames[K_COUNT] = {
-    "bisect_prep",  "bisect",       "band_from_dense", "tridiag_extract", "band_chase",
+    "bisect_prep",  "bisect",       "band_from_dense", "tridiag_extract", "band_chase", "band_tri",
     "tsqr_leaf_qr", "tsqr_node_qr", "tsqr_node_apply", "tsqr_leaf_apply", "recon_lu",
     "recon_u2",     "symm",         "vform_xt",        "vform_utx",       "vform_reduce",
     "vform_v",      "syr2k",        "split_bf16",      "syr2k_tc",        "symm_tc",
@@ -90,20 +90,30 @@ static int default_b0(int n, int prec) {
     return n >= 12288 ? 128 : (n >= 1024 ? 64 : 32);
 }
 
-static int schedule(int b0, int *out) {
+// Band schedule (Algorithm 4.3 with k = 2 halvings): b0 -> b0/2 -> ...
+// until b <= 32 is a power of two, which then goes to 1 in one stage (k = b,
+// the larger reduction factor the paper allows per stage); an odd b also
+// finishes with b -> 1.
+static int schedule(int b0, int elem, int *out) {
     int k = 0;
     out[k++] = b0;
     while (out[k - 1] > 1) {
         const int b = out[k - 1];
-        out[k++] = (b % 2 == 0) ? b / 2 : 1;
+        out[k++] = (band_tri_supported(b, elem) || b % 2 != 0) ? 1 : b / 2;
     }
     return k;
 }
 
 template <typename T>
+static int band_stage(sev_ctx *h, int n, T *AB, int ldab, int b, int hh, void *ws, size_t ws_bytes) {
+    if (hh == 1 && band_tri_supported(b, (int)sizeof(T))) return launch_band_tri<T>(h, n, AB, ldab, b, ws, ws_bytes);
+    return launch_band_to_band<T>(h, n, AB, ldab, b, hh, ws, ws_bytes);
+}
+
+template <typename T>
 static size_t eig_workspace(sev_ctx *h, int n, int b0) {
     int sched[40];
-    const int ns = schedule(b0, sched);
+    const int ns = schedule(b0, (int)sizeof(T), sched);
     const int ldab = 2 * b0 > 2 ? 2 * b0 : 2;
     size_t stage = bisect_workspace(n);
     if (b0 < n - 1) {
@@ -114,6 +124,7 @@ static size_t eig_workspace(sev_ctx *h, int n, int b0) {
         const size_t w = band_workspace(n, sched[s], sched[s + 1]);
         if (w > stage) stage = w;
     }
+    if (band_tri_workspace(n) > stage) stage = band_tri_workspace(n);
     Carver c(nullptr);
     c.take<T>((size_t)ldab * n);
     c.take<double>((size_t)n);
@@ -126,9 +137,11 @@ template <typename T>
 static int eigvalsh_t(sev_ctx *h, int n, T *A, int lda, int b0, double *eigs) {
     if (b0 > n - 1) b0 = n - 1 > 1 ? n - 1 : 1;
     int sched[40];
-    const int ns = schedule(b0, sched);
+    const int ns = schedule(b0, (int)sizeof(T), sched);
     for (int s = 0; s + 1 < ns; ++s)
-        if (band_smem_bytes<T>(sched[s], sched[s + 1]) > h->smem_optin) return SEV_ERR_UNSUPPORTED;
+        if (!(sched[s + 1] == 1 && band_tri_supported(sched[s], (int)sizeof(T))) &&
+            band_smem_bytes<T>(sched[s], sched[s + 1]) > h->smem_optin)
+            return SEV_ERR_UNSUPPORTED;
     const int ldab = 2 * b0 > 2 ? 2 * b0 : 2;
     void *ws = nullptr;
     const size_t need = eig_workspace<T>(h, n, b0);
@@ -147,7 +160,7 @@ static int eigvalsh_t(sev_ctx *h, int n, T *A, int lda, int b0, double *eigs) {
     }
     if (rc) return rc;
     for (int s = 0; s + 1 < ns; ++s) {
-        rc = launch_band_to_band<T>(h, n, AB, ldab, sched[s], sched[s + 1], stage, stage_bytes);
+        rc = band_stage<T>(h, n, AB, ldab, sched[s], sched[s + 1], stage, stage_bytes);
         if (rc) return rc;
     }
     rc = launch_tridiag_extract<T>(h, n, AB, ldab, d, e);
@@ -323,14 +336,15 @@ int sev_band_to_band(sev_handle h, int n, void *AB, int ldab, int b, int hh, int
     if (prec != SEV_FP64 && prec != SEV_MIXED) return -7;
     if (n == 0) return SEV_OK;
     if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
-    if ((prec == SEV_FP64 ? band_smem_bytes<double>(b, hh) : band_smem_bytes<float>(b, hh)) > h->smem_optin)
+    const bool tri = hh == 1 && band_tri_supported(b, prec == SEV_FP64 ? 8 : 4);
+    if (!tri && (prec == SEV_FP64 ? band_smem_bytes<double>(b, hh) : band_smem_bytes<float>(b, hh)) > h->smem_optin)
         return SEV_ERR_UNSUPPORTED;
-    const size_t need = band_workspace(n, b, hh);
+    const size_t need = tri ? band_tri_workspace(n) : band_workspace(n, b, hh);
     void *ws = nullptr;
     int rc = get_workspace(h, need, &ws);
     if (rc) return rc;
-    return prec == SEV_FP64 ? launch_band_to_band<double>(h, n, (double *)AB, ldab, b, hh, ws, need)
-                            : launch_band_to_band<float>(h, n, (float *)AB, ldab, b, hh, ws, need);
+    return prec == SEV_FP64 ? band_stage<double>(h, n, (double *)AB, ldab, b, hh, ws, need)
+                            : band_stage<float>(h, n, (float *)AB, ldab, b, hh, ws, need);
 }
 
 int sev_tridiag_bisect(sev_handle h, int n, const double *d, const double *e, double rtol, double *eigs) {

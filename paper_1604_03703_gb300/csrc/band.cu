@@ -126,10 +126,9 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     const int tid = threadIdx.x, nt = blockDim.x;
 
     // 1. QR of the n_r x h block
-    for (int idx = tid; idx < n_r * h; idx += nt) {
-        const int r = idx % n_r, c = idx / n_r;
-        S.Xs[r + (size_t)c * ldb1] = bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad);
-    }
+    batched_copy<T>(
+        n_r * h, tid, nt, [&](int k) { return bld(AB, ldab, n, o_qr_r + k % n_r, o_qr_c + k / n_r, bad); },
+        [&](int k, T v) { S.Xs[k % n_r + (size_t)(k / n_r) * ldb1] = v; });
     __syncthreads();
     const int nr = cta_qr(n_r, h, S.Xs, ldb1, S.tau, S.red);
     // 2. B[qr rows, qr cols] = [R; 0]
@@ -148,10 +147,9 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     cta_gemm<T, false, false>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, T(0), S.UTs, ldb1);
     __syncthreads();
     // 4. the qr-row diagonal block X_d (n_r x n_r): two-sided update
-    for (int idx = tid; idx < n_r * n_r; idx += nt) {
-        const int r = idx % n_r, c = idx / n_r;
-        S.Xs[r + (size_t)c * ldb1] = bld_sym(AB, ldab, n, o_qr_r + r, o_qr_r + c, bad);
-    }
+    batched_copy<T>(
+        n_r * n_r, tid, nt, [&](int k) { return bld_sym(AB, ldab, n, o_qr_r + k % n_r, o_qr_r + k / n_r, bad); },
+        [&](int k, T v) { S.Xs[k % n_r + (size_t)(k / n_r) * ldb1] = v; });
     __syncthreads();
     // W_d = X_d (U T)
     cta_gemm<T, false, false>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
@@ -189,10 +187,10 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         const int a_end = part == 0 ? o_v : n_c;
         for (int a0 = a_begin; a0 < a_end; a0 += b) {
             const int rows = min(b, a_end - a0);
-            for (int idx = tid; idx < rows * n_r; idx += nt) {
-                const int r = idx % rows, c = idx / rows;
-                S.Xs[r + (size_t)c * ldb1] = bld_sym(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, bad);
-            }
+            batched_copy<T>(
+                rows * n_r, tid, nt,
+                [&](int k) { return bld_sym(AB, ldab, n, o_up_c + a0 + k % rows, o_qr_r + k / rows, bad); },
+                [&](int k, T v) { S.Xs[k % rows + (size_t)(k / rows) * ldb1] = v; });
             __syncthreads();
             cta_gemm<T, false, false>(rows, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
             __syncthreads();
@@ -230,13 +228,13 @@ __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int 
             if (i > 1) {
                 if (threadIdx.x == 0) {
                     const int need = min(j + 2, Jprev);
-                    long it = 0;
+                    const long long t0 = clock64();
                     while (ld_acquire(&progress[s - 1]) < need) {
                         if (*(volatile int *)err != 0) {
                             s_abort = 1;
                             break;
                         }
-                        if (++it > kSpinCap / 8) {
+                        if (wait_expired(t0)) {
                             latch_error(err, SEV_ERR_TIMEOUT);
                             s_abort = 1;
                             break;

@@ -1,0 +1,496 @@
+// band_tri.cu -- the last band reduction, b -> 1 (Algorithm 4.2 with k = b,
+// h = 1), for b <= 32, as a sliding-window bulge chase.
+//
+// With h = 1 every chase (i, j) is ONE Householder reflector: it
+// annihilates the single column o_qr.c below row o_qr.r (o_qr.r =
+// i + (j-1) b, o_qr.c = o_qr.r - 1 for j = 1, o_qr.r - b for j > 1) and
+// applies H two-sidedly to the qr rows [o_qr.r, o_qr.r + n_r) against the
+// update rows [o_up.c, o_up.c + n_c) (o_up.c = o_qr.r for j = 1,
+// o_qr.r - b + 1 for j > 1; n_c = min(n - o_up.c, 2b) resp. 3b - 1).  One
+// warp performs a chase: lane l owns one update row above, in, and below
+// the qr rows; off rows get X <- X H (row-local), the qr-row block gets
+// H X H = X - v w^T - w v^T with p = tau X v, w = p - (tau/2)(p^T v) v.
+//
+// Schedule.  A CTA takes G consecutive sweeps (warp g -> sweep i0 + g) and
+// steps them together: at step t warp g performs chase t - 3g, so sweep i
+// runs 3 chases behind sweep i - 1 -- the rule that chase (i, j) follows
+// (i - 1, j + 2) -- and the chases of one step are independent.  Steps are
+// separated by __syncthreads.  The band columns the group touches live in a
+// shared-memory ring of (3G + 1) b + 2 columns (2b diagonals each): columns
+// are loaded from global memory as warp 0 reaches them and written back
+// once the group's last sweep has passed them (after its chase j, columns
+// below o_qr.r(i_last, j) are final).  The group then publishes j with a
+// release store; the next group waits (acquire, capped) for j + 2 before
+// loading a column range -- the only global synchronisation, once per step
+// per group boundary.  Groups are handed out in order by a global counter
+// and each CTA finishes its group before taking another, so every awaited
+// group is held by a running CTA.
+#include "common.cuh"
+
+#ifdef SEV_TRACE
+static __device__ long long *sev_trace_buf = nullptr;
+static __device__ int sev_trace_phase_on = 0;
+static __device__ long long sev_trace_phase[8];
+extern "C" int sev_trace_set(void *p) {
+    return cudaMemcpyToSymbol(sev_trace_buf, &p, sizeof(p)) == cudaSuccess ? 0 : 1;
+}
+#define TRACE(gi, t, k, v)                                                                    \
+    do {                                                                                      \
+        if (sev_trace_buf && (gi) < 4 && (t) < 4096) sev_trace_buf[((gi) * 4096 + (t)) * 8 + (k)] = (v); \
+    } while (0)
+#define TRACEP(k)                                                                      \
+    do {                                                                               \
+        if (sev_trace_phase_on == (int)blockIdx.x + 1 && (threadIdx.x & 31) == 0 && (threadIdx.x >> 5) == 0) \
+            sev_trace_phase[(k)] = clock64();                                          \
+    } while (0)
+#else
+#define TRACEP(k) \
+    do {          \
+    } while (0)
+#define TRACE(gi, t, k, v) \
+    do {                   \
+    } while (0)
+#endif
+
+namespace sev {
+
+constexpr int kTriInf = 1 << 30;
+
+__device__ __forceinline__ int ld_acquire_i(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_i(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__host__ __device__ __forceinline__ int tri_chases(int n, int b, int i) {
+    const int r = n - i;
+    return r < 2 ? 0 : (n - 2 - i) / b + 1;
+}
+
+template <typename T, int B>
+struct TriWin {
+    T *w;      // ring of WCAP columns x LDW diagonals
+    int wcap;  // columns in the ring
+    static constexpr int LDW = 2 * B;
+    __device__ __forceinline__ T &at(int r, int c) const {  // r >= c, r - c < 2B
+        return w[(c % wcap) * LDW + (r - c)];
+    }
+    __device__ __forceinline__ T &sym(int u, int q) const { return u >= q ? at(u, q) : at(q, u); }
+};
+
+// Reflector scalars from this lane's x (lanes t < nr hold x_t): pair-float
+// sum of squares over the B-lane group, FP64 scalars computed by every lane
+// (no divergence; an FP64 instruction costs the same for 1 or 32 lanes).
+template <typename T, int B>
+__device__ __forceinline__ void tri_reflector(T x, int nr, T &v, T &tau, T &beta) {
+    constexpr int W = B < 32 ? B : 32;
+    const int lane = threadIdx.x & 31;
+    double ssq;
+    if (sizeof(T) == 4) {
+        F2 acc{0.f, 0.f};
+        if (lane >= 1 && lane < nr) f2_add_sq(acc, (float)x);
+        acc = warp_sum_f2<W>(acc);
+        ssq = (double)acc.hi + (double)acc.lo;
+    } else {
+        const double xd = (lane >= 1 && lane < nr) ? (double)x : 0.0;
+        double a = xd * xd;
+#pragma unroll
+        for (int off = W / 2; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        ssq = a;
+    }
+    const double alpha = (double)__shfl_sync(0xffffffffu, x, 0);
+    double td, bd, id;
+    house_scalars(alpha, ssq, &td, &bd, &id);
+    tau = (T)td;
+    beta = (T)bd;
+    v = lane == 0 ? T(1) : (lane < nr ? x * (T)id : T(0));
+}
+
+// One chase (i, j), h = 1, by one warp on the shared window, with the rows a
+// lane owns held in registers: lane l owns update row up0 + l above the qr
+// rows, qr row o + l and row o + n_r + l below them.  The reflector (v in
+// lane t, tau, beta) arrives in registers; if the sweep has a next chase,
+// its reflector -- a function of column o after this chase only -- is formed
+// here and returned the same way (its column gets [beta'; 0]).
+template <typename T, int B>
+__device__ __forceinline__ void tri_chase(int n, int o, int j, bool has_next, const TriWin<T, B> &W, T *vbuf,
+                                          T *wbuf, T &v, T &tau, T &beta) {
+    constexpr int LDW = 2 * B;
+    const int lane = threadIdx.x & 31;
+    const int wcap = W.wcap;
+    T *const w = W.w;
+    const int n_r = min(n - o, B);
+    int up0, nc, ov;
+    if (j == 1) {
+        up0 = o;
+        nc = min(n - o, 2 * B);
+        ov = 0;
+    } else {
+        up0 = o - B + 1;
+        nc = min(n - up0, 3 * B - 1);
+        ov = B - 1;
+    }
+    const int so = o % wcap;
+    auto cslot = [&](int q) {  // slot of column o + q (q < B)
+        const int sl = so + q;
+        return sl >= wcap ? sl - wcap : sl;
+    };
+    TRACEP(0);
+    // broadcast v
+    if (lane < B) vbuf[lane] = v;
+    __syncwarp();
+    T vv[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) vv[q] = q < n_r ? vbuf[q] : T(0);
+    const T tt = tau;
+    // load the owned rows (all loads in flight before any use)
+    const bool has_a = lane < ov;
+    const int ua = up0 + lane;  // above: entries (o + q, ua), column ua
+    T *rowa = w + (size_t)((has_a ? ua : o) % wcap) * LDW + (o - (has_a ? ua : o));
+    const int ub = o + n_r + lane;  // below: entries (ub, o + q)
+    const bool has_b = lane < B && ub < up0 + nc;
+    const bool has_d = lane < n_r;  // diag: entries of qr row o + lane
+    const int sd = cslot(lane < B ? lane : 0);
+    T ra[B], rb[B], rd[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        ra[q] = (has_a && q < n_r) ? rowa[q] : T(0);
+        rb[q] = (has_b && q < n_r) ? w[(size_t)cslot(q) * LDW + (ub - o - q)] : T(0);
+        T dv = T(0);
+        if (has_d && q < n_r) dv = q <= lane ? w[(size_t)cslot(q) * LDW + (lane - q)] : w[(size_t)sd * LDW + (q - lane)];
+        rd[q] = dv;
+    }
+    TRACEP(1);
+    // off rows: X <- X (I - tau v v^T)
+    T sa = 0, sb = 0, p = 0;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        sa = fma(ra[q], vv[q], sa);
+        sb = fma(rb[q], vv[q], sb);
+        p = fma(rd[q], vv[q], p);
+    }
+    sa *= tt;
+    sb *= tt;
+    p *= tt;
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        ra[q] = fma(-sa, vv[q], ra[q]);
+        rb[q] = fma(-sb, vv[q], rb[q]);
+    }
+    TRACEP(2);
+    // the next chase's reflector: column o of the rows below, x_t = rb[0] of lane t
+    T nv = T(0), ntau = T(0), nbeta = T(0);
+    const int n_r_next = has_next ? min(n - (o + B), B) : 0;
+    if (has_next) tri_reflector<T, B>(rb[0], n_r_next, nv, ntau, nbeta);
+    TRACEP(3);
+    // qr-row block: H X H = X - v w^T - w v^T, w = p - (tau/2)(p^T v) v
+    const T vl = lane < n_r ? v : T(0);  // this lane's own v (a runtime index into vv would spill)
+    T ptv = has_d ? p * vl : T(0);
+#pragma unroll
+    for (int off = (B < 32 ? B : 32) / 2; off > 0; off >>= 1) ptv += __shfl_xor_sync(0xffffffffu, ptv, off);
+    const T wl = p - T(0.5) * tt * ptv * vl;
+    if (lane < B) wbuf[lane] = wl;
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const T wq = wbuf[q];
+        rd[q] = fma(-vl, wq, fma(-wl, vv[q], rd[q]));
+    }
+    TRACEP(4);
+    // store back (the next reflector's column gets [beta'; 0])
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        if (has_a && q < n_r) rowa[q] = ra[q];
+        if (has_b && q < n_r) {
+            T val = rb[q];
+            if (q == 0 && has_next && lane < n_r_next) val = lane == 0 ? nbeta : T(0);
+            w[(size_t)cslot(q) * LDW + (ub - o - q)] = val;
+        }
+        if (has_d && q < n_r && q <= lane) w[(size_t)cslot(q) * LDW + (lane - q)] = rd[q];
+    }
+    __syncwarp();
+    TRACEP(5);
+    v = nv;
+    tau = ntau;
+    beta = nbeta;
+}
+
+// G compute warps + one loader warp + one writer warp, decoupled through
+// shared-memory flags.  Compute warps step together (named barrier 1): at
+// step t warp g performs chase t - 3g once the loader has made step t's
+// columns available (s_avail >= t).  The loader runs ahead: it polls the
+// previous group (acquire, capped, cached), waits for ring space (columns
+// written back, s_wblo) and loads each step's new columns.  The writer runs
+// behind: once compute has finished a step (s_done), it writes back every
+// column that became final, advances s_wblo and publishes the group's
+// progress (release store).  Flags are ordered with block-scope fences; each
+// wait is capped and an abort turns the remaining steps into no-ops so that
+// every warp still reaches its barriers.  The ring holds (3G + 3) b + 2
+// columns.
+template <int B, int G>
+__host__ __device__ constexpr int tri_wcap() {
+    return (3 * G + 3) * B + 2;
+}
+
+__device__ __forceinline__ void named_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <typename T, int B, int G>
+__global__ void __launch_bounds__((G + 2) * 32, 1)
+    band_tri_kernel(int n, T *AB, int ldab, int nsweeps, int ngroups, int *progress, int *group_ctr, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int LDW = 2 * B;
+    constexpr int wcap = tri_wcap<B, G>();
+    TriWin<T, B> W;
+    W.w = (T *)smem;
+    W.wcap = wcap;
+    T *vb = W.w + (size_t)wcap * LDW;  // G x 32
+    T *wb = vb + G * 32;               // G x 32
+    __shared__ int s_group;
+    __shared__ volatile int s_abort, s_avail, s_done, s_wblo;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool loader = warp == G, writer = warp == G + 1;
+
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int g = atomicAdd(group_ctr, 1);
+            s_group = g;
+            s_abort = 0;
+            s_avail = 0;
+            s_done = 0;
+            s_wblo = 1 + g * G - 1;
+        }
+        __syncthreads();
+        const int gi = s_group;
+        if (gi >= ngroups) break;
+        const int i0 = 1 + gi * G;
+        const int nact = min(G, nsweeps - i0 + 1);
+        const int il = i0 + nact - 1;
+        const int Jf = tri_chases(n, B, i0), Jl = tri_chases(n, B, il);
+        const int Jprev = gi > 0 ? tri_chases(n, B, i0 - 1) : 0;
+        const int tmax = Jl + 3 * (nact - 1);
+        auto hi_of = [&](int ts) { return (ts >= Jf) ? n : min(n, i0 + ts * B); };
+
+        if (warp < G) {
+            // ------------------------------------------------------ compute
+            T rv = T(0), rtau = T(0), rbeta = T(0);  // this warp's pending reflector
+            for (int t = 1; t <= tmax; ++t) {
+                if (warp == 0 && lane == 0) TRACE(gi, t, 0, clock64());
+                if (warp == 0 && lane == 0 && !s_abort) {
+                    const int need = min(t, Jf);
+                    const long long t0 = clock64();
+                    while (s_avail < need && !s_abort) {
+                        if (wait_expired(t0)) {
+                            latch_error(err, SEV_ERR_TIMEOUT);
+                            s_abort = 1;
+                        }
+                    }
+                    __threadfence_block();
+                }
+                named_bar(1, G * 32);
+                if (warp == 0 && lane == 0) TRACE(gi, t, 1, clock64());
+                if (!s_abort) {
+                    const int j = t - 3 * warp;
+                    const int i = i0 + warp;
+                    const int Ji = tri_chases(n, B, i);
+                    if (warp < nact && j >= 1 && j <= Ji) {
+                        const int o = i + (j - 1) * B;
+                        if (j == 1) {
+                            // the sweep's first reflector: column i - 1, rows [i, i + n_r)
+                            const int nr1 = min(n - o, B);
+                            T *xcol = W.w + (size_t)((o - 1) % wcap) * LDW + 1;
+                            const T x = lane < nr1 ? xcol[lane] : T(0);
+                            tri_reflector<T, B>(x, nr1, rv, rtau, rbeta);
+                            if (lane < nr1) xcol[lane] = lane == 0 ? rbeta : T(0);
+                            __syncwarp();
+                        }
+#ifdef SEV_TRACE
+                        if (warp == 0 && lane == 0 && gi == 1 && j == 40) sev_trace_phase_on = blockIdx.x + 1;
+                        __syncwarp();
+#endif
+                        tri_chase<T, B>(n, o, j, j < Ji, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
+#ifdef SEV_TRACE
+                        if (warp == 0 && lane == 0 && gi == 1 && j == 40 && sev_trace_buf)
+                            for (int k = 0; k < 6; ++k) sev_trace_buf[3 * 4096 * 8 + 4000 * 8 + k] = sev_trace_phase[k];
+                        if (warp == 0 && lane == 0 && gi == 1 && j == 40) sev_trace_phase_on = 0;
+#endif
+                    }
+                }
+                if (lane == 0) TRACE(gi, t, 3 + (warp < 3 ? warp : 2), clock64());
+                named_bar(1, G * 32);
+                if (warp == 0 && lane == 0) {
+                    TRACE(gi, t, 2, clock64());
+                    __threadfence_block();
+                    s_done = t;
+                }
+            }
+        } else if (loader) {
+            // ------------------------------------------------------- loader
+            int loaded_hi = i0 - 1, seen = 0;
+            for (int ts = 1; ts <= Jf && !s_abort; ++ts) {
+                if (gi > 0 && ts + 2 > seen) {
+                    const int need = (ts + 2 <= Jprev) ? ts + 2 : kTriInf;
+                    int pv = 0;
+                    if (lane == 0) {
+                        const long long t0 = clock64();
+                        unsigned ns = 32;
+                        while ((pv = ld_acquire_i(&progress[gi - 1])) < need) {
+                            if (*(volatile int *)err != 0 || s_abort) {
+                                pv = -1;
+                                break;
+                            }
+                            if (wait_expired(t0)) {
+                                latch_error(err, SEV_ERR_TIMEOUT);
+                                pv = -1;
+                                break;
+                            }
+                            __nanosleep(ns);
+                            if (ns < 512) ns <<= 1;
+                        }
+                    }
+                    pv = __shfl_sync(0xffffffffu, pv, 0);
+                    if (pv < 0) {
+                        if (lane == 0) s_abort = 1;
+                        break;
+                    }
+                    seen = pv;
+                    if (lane == 0) TRACE(gi, ts, 6, clock64());
+                }
+                const int hi = hi_of(ts);
+                // ring space: columns below hi - wcap must have been written back
+                if (lane == 0) {
+                    const long long t0 = clock64();
+                    while (s_wblo < hi - wcap && !s_abort) {
+                        if (wait_expired(t0)) {
+                            latch_error(err, SEV_ERR_TIMEOUT);
+                            s_abort = 1;
+                        }
+                    }
+                    __threadfence_block();
+                }
+                __syncwarp();
+                if (s_abort) break;
+                {
+                    const int c0 = loaded_hi;
+                    batched_copy<T, 16>(
+                        (hi - c0) * LDW, lane, 32,
+                        [&](int k) {
+                            const int c = c0 + k / LDW, d = k % LDW;
+                            return (c + d < n) ? __ldcg(AB + d + (size_t)c * ldab) : T(0);
+                        },
+                        [&](int k, T v) { W.w[((c0 + k / LDW) % wcap) * LDW + k % LDW] = v; });
+                }
+                loaded_hi = max(loaded_hi, hi);
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    s_avail = ts;
+                    TRACE(gi, ts, 7, clock64());
+                }
+            }
+        } else if (writer) {
+            // ------------------------------------------------------- writer
+            int wb_lo = i0 - 1, written = 0;
+            while (written < tmax) {
+                int ts = 0;
+                if (lane == 0) {
+                    const long long t0 = clock64();
+                    while ((ts = s_done) <= written && !s_abort) {
+                        if (wait_expired(t0)) {
+                            latch_error(err, SEV_ERR_TIMEOUT);
+                            s_abort = 1;
+                        }
+                    }
+                    __threadfence_block();
+                }
+                ts = __shfl_sync(0xffffffffu, ts, 0);
+                if (s_abort) break;
+                written = ts;
+                const int jl = ts - 3 * (nact - 1);
+                if (jl < 1) continue;
+                const bool done = jl >= Jl;
+                const int fin = done ? n : min(n, il + (jl - 1) * B);
+                for (int idx = lane; idx < (fin - wb_lo) * LDW; idx += 32) {
+                    const int c = wb_lo + idx / LDW, d = idx % LDW;
+                    if (c + d < n) AB[d + (size_t)c * ldab] = W.w[(c % wcap) * LDW + d];
+                }
+                if (fin > wb_lo) wb_lo = fin;
+                __syncwarp();
+                if (lane == 0) {
+                    __threadfence_block();
+                    s_wblo = wb_lo;
+                    // the release store orders the warp's write-back before the flag
+                    st_release_i(&progress[gi], done ? kTriInf : jl);
+                }
+            }
+        }
+        __syncthreads();
+        if (s_abort) return;
+    }
+}
+
+template <typename T, int B, int G>
+static int launch_tri(sev_ctx *h, int n, T *AB, int ldab, int *progress, int *ctr, int nsweeps) {
+    const int ngroups = (nsweeps + G - 1) / G;
+    constexpr int wcap = tri_wcap<B, G>();
+    const size_t smem = sizeof(T) * ((size_t)wcap * 2 * B + 2 * G * 32);
+    if (smem > h->smem_optin) return SEV_ERR_UNSUPPORTED;
+    SEV_CUDA(cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)ngroups, h->stream));
+    SEV_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), h->stream));
+    auto kern = band_tri_kernel<T, B, G>;
+    SEV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (G + 2) * 32, smem));
+    if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
+    // groups start ~3G steps apart and each runs ~J + 3G steps, so about
+    // J / (3G) of them are busy at once; more CTAs would only poll
+    const int J1 = tri_chases(n, B, 1);
+    int grid = h->sm_count * per_sm;
+    const int busy = J1 / (3 * G) + 16;
+    if (grid > busy) grid = busy;
+    if (grid > ngroups) grid = ngroups;
+    SEV_LAUNCH(h, K_BAND_TRI, kern, grid, (G + 2) * 32, smem, n, AB, ldab, nsweeps, ngroups, progress, ctr,
+               h->d_err);
+    return SEV_OK;
+}
+
+int band_tri_supported(int b, int elem) { return b == 2 || b == 4 || b == 8 || b == 16 || (b == 32 && elem == 4); }
+
+size_t band_tri_workspace(int n) {
+    Carver c(nullptr);
+    c.take<int>((size_t)n + 1);
+    c.take<int>(1);
+    return c.bytes();
+}
+
+template <typename T>
+int launch_band_tri(sev_ctx *h, int n, T *AB, int ldab, int b, void *ws, size_t ws_bytes) {
+    const int nsweeps = n >= 3 ? n - 2 : 0;
+    if (nsweeps <= 0) return SEV_OK;
+    if (ws_bytes < band_tri_workspace(n)) return SEV_ERR_WORKSPACE;
+    Carver c(ws);
+    int *progress = c.take<int>((size_t)n + 1);
+    int *ctr = c.take<int>(1);
+    switch (b) {
+        case 2: return launch_tri<T, 2, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 4: return launch_tri<T, 4, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 8: return launch_tri<T, 8, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 16:
+            if constexpr (sizeof(T) == 8) return launch_tri<T, 16, 7>(h, n, AB, ldab, progress, ctr, nsweeps);
+            return launch_tri<T, 16, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 32:
+            if constexpr (sizeof(T) == 4) return launch_tri<T, 32, 7>(h, n, AB, ldab, progress, ctr, nsweeps);
+            return SEV_ERR_UNSUPPORTED;
+        default: return SEV_ERR_UNSUPPORTED;
+    }
+}
+
+template int launch_band_tri<float>(sev_ctx *, int, float *, int, int, void *, size_t);
+template int launch_band_tri<double>(sev_ctx *, int, double *, int, int, void *, size_t);
+
+}  // namespace sev

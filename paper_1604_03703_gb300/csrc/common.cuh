@@ -22,6 +22,7 @@ enum KernelId {
     K_BAND_FROM_DENSE,
     K_TRIDIAG_EXTRACT,
     K_BAND_CHASE,
+    K_BAND_TRI,
     K_TSQR_LEAF,
     K_TSQR_TREE,
     K_TSQR_DOWN,
@@ -115,6 +116,9 @@ __device__ __forceinline__ void latch_error(int *err, int code) { atomicCAS(err,
 
 constexpr int kThreads = 256;
 constexpr long kSpinCap = 20000000;  // ~ a few seconds of polling with back-off
+// Time limit of every device-side wait, in SM clock cycles (~2 s at 2 GHz).
+constexpr long long kWaitCycles = 4000000000LL;
+__device__ __forceinline__ bool wait_expired(long long t0) { return clock64() - t0 > kWaitCycles; }
 
 // ------------------------------------------------------ reductions (CTA-wide)
 __device__ __forceinline__ double warp_sum(double v) {
@@ -155,81 +159,211 @@ __device__ __forceinline__ double block_max(double v, double *red) {
 }
 
 // ------------------------------------------------------------- Householder
-// Reflector of the column segment x[0..m-1] (shared memory, stride 1), in
-// the "always reflect" convention: beta = -sgn(alpha)||x|| (sgn(0) = +1),
-// tau = (beta - alpha)/beta in [1, 2]; zero vector -> tau = beta = 0.  The
-// norm, beta and tau are computed in FP64 whatever T is.  x[1..m-1] is
-// scaled in place to v[1..m-1] (v[0] = 1 implicit); x[0] is NOT modified.
-// Ends with a __syncthreads (scaled vector visible to the CTA).
+// On this part every FP64 instruction has ~64 cycles of latency and an IEEE
+// FP64 division or square root ~650, so the reflector scalars below avoid
+// both while staying FP64-accurate:
+//  * the sum of squares of FP32 data is accumulated as an unevaluated pair
+//    of floats with error-free transformations (x^2 split exactly by an FMA,
+//    Knuth's TwoSum for the additions), reduced across the warp in that
+//    form and finished in FP64 -- the relative error is ~2^-44, far below
+//    what the FP64 scalars need;
+//  * 1/||x|| and 1/(alpha - beta) come from an FP32 hardware seed refined by
+//    two Newton steps in FP64 (y <- y + y(1 - s y^2)/2 and
+//    r <- r + r(1 - d r)): 22 correct bits become full double precision.
+struct F2 {
+    float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {  // TwoSum of the leading parts, then renormalise
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = e + a.lo + b.lo;
+    const float hi = s + lo;
+    return {hi, lo - (hi - s)};
+}
+__device__ __forceinline__ void f2_add_sq(F2 &a, float x) {
+    const float p = x * x;
+    const float pe = fmaf(x, x, -p);  // x^2 = p + pe exactly
+    a = f2_add(a, F2{p, pe});
+}
+template <int WIDTH = 32>
+__device__ __forceinline__ F2 warp_sum_f2(F2 v) {
+#pragma unroll
+    for (int o = WIDTH / 2; o > 0; o >>= 1) {
+        F2 w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = f2_add(v, w);
+    }
+    return v;
+}
+
+// 2^k for |k| < 1000, by building the exponent field.
+__device__ __forceinline__ double pow2i(int k) { return __hiloint2double((1023 + k) << 20, 0); }
+
+// Householder scalars in FP64 from alpha = x_0 and ssq = sum_{i>0} x_i^2:
+// beta = -sgn(alpha) sqrt(alpha^2 + ssq) (sgn(0) = +1), tau = (beta - alpha)/beta,
+// inv = 1/(alpha - beta); a zero vector gives tau = beta = inv = 0.
+__device__ __forceinline__ void house_scalars(double alpha, double ssq, double *tau, double *beta, double *inv) {
+    const double s = fma(alpha, alpha, ssq);
+    if (!(s > 0.0)) {
+        *tau = *beta = *inv = 0.0;
+        return;
+    }
+    // seed for s^(-1/2): s = m 2^(2k), m in [2^-2, 2^2)
+    const int e = ((__double2hiint(s) >> 20) & 0x7ff) - 1023;
+    const int k = e >> 1;
+    const double m = s * pow2i(-2 * k);
+    double y = (double)rsqrtf((float)m) * pow2i(-k);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double t = s * y;
+        const double eps = fma(-t, y, 1.0);  // 1 - s y^2
+        y = fma(0.5 * y, eps, y);
+    }
+    double nrm = s * y;
+    nrm = fma(0.5 * y, fma(-nrm, nrm, s), nrm);  // one correction of the square root itself
+    const double aa = fabs(alpha);
+    *beta = alpha < 0.0 ? nrm : -nrm;
+    const double d = aa + nrm;  // |alpha - beta|
+    *tau = d * y;               // (nrm + |alpha|) / nrm
+    // 1/d: seed from FP32 on the scaled value, two Newton steps
+    const int ed = ((__double2hiint(d) >> 20) & 0x7ff) - 1023;
+    const double dm = d * pow2i(-ed);
+    double r = (double)(1.0f / (float)dm) * pow2i(-ed);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) r = fma(r, fma(-d, r, 1.0), r);
+    *inv = alpha < 0.0 ? -r : r;  // alpha - beta = sgn(alpha) d
+}
+
+// Reflector of the column segment x[0..m-1] (shared memory, stride 1),
+// computed by ONE warp, in the "always reflect" convention:
+// beta = -sgn(alpha)||x|| (sgn(0) = +1), tau = (beta - alpha)/beta in [1, 2];
+// a zero vector gives tau = beta = 0.  Norm, beta and tau are FP64-accurate
+// (see above); the scalars are formed in lane 0 and broadcast.  On return
+// x[1..m-1] holds v[1..m-1] (v[0] = 1 implicit), x[0] = beta and
+// *tau_out = tau.
 template <typename T>
-__device__ void cta_house(int m, T *x, double *red, double *tau_out, double *beta_out) {
+__device__ double warp_house(int m, T *x, T *tau_out) {
+    const int lane = threadIdx.x & 31;
     const double alpha = (double)x[0];
-    double ssq = 0.0;
-    for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
-        double t = (double)x[i];
-        ssq += t * t;
-    }
-    ssq = block_sum(ssq, red);
-    double scale = 1.0;
-    if (sizeof(T) == 8 && ((ssq != 0.0 && ssq < 1e-280) || !(ssq < 1e300) || fabs(alpha) > 1e150)) {
-        // rare path: rescale by an exact power of two so squares neither
-        // overflow nor underflow
-        double amax = fabs(alpha);
-        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) amax = fmax(amax, fabs((double)x[i]));
-        amax = block_max(amax, red);
-        int e2;
-        frexp(amax, &e2);
-        scale = ldexp(1.0, -e2);
-        ssq = 0.0;
-        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) {
-            double t = (double)x[i] * scale;
-            ssq += t * t;
-        }
-        ssq = block_sum(ssq, red);
-    }
-    double tau, beta;
-    if (ssq == 0.0 && alpha == 0.0) {
-        tau = 0.0;
-        beta = 0.0;
+    double ssq;
+    if (sizeof(T) == 4) {
+        F2 acc{0.f, 0.f};
+        for (int i = 1 + lane; i < m; i += 32) f2_add_sq(acc, (float)x[i]);
+        acc = warp_sum_f2(acc);
+        ssq = (double)acc.hi + (double)acc.lo;
     } else {
-        const double as = alpha * scale;
-        const double nrm = sqrt(as * as + ssq) / scale;
-        beta = alpha < 0.0 ? nrm : -nrm;
-        tau = (beta - alpha) / beta;
-        const double inv = 1.0 / (alpha - beta);
-        for (int i = 1 + threadIdx.x; i < m; i += blockDim.x) x[i] = (T)((double)x[i] * inv);
+        double a = 0.0;
+        for (int i = 1 + lane; i < m; i += 32) {
+            const double t = (double)x[i];
+            a = fma(t, t, a);
+        }
+        ssq = warp_sum(a);
+        if ((ssq != 0.0 && ssq < 1e-280) || !(ssq < 1e300) || fabs(alpha) > 1e150 ||
+            (alpha != 0.0 && fabs(alpha) < 1e-140)) {
+            // rare path for FP64 data: rescale by an exact power of two
+            double amax = fabs(alpha);
+            for (int i = 1 + lane; i < m; i += 32) amax = fmax(amax, fabs((double)x[i]));
+            amax = warp_max(amax);
+            int e2;
+            frexp(amax, &e2);
+            const double sc = ldexp(1.0, -e2);
+            double a2 = 0.0;
+            for (int i = 1 + lane; i < m; i += 32) {
+                const double t = (double)x[i] * sc;
+                a2 = fma(t, t, a2);
+            }
+            a2 = warp_sum(a2);
+            double tau = 0.0, beta = 0.0, inv = 0.0;
+            if (lane == 0) house_scalars(alpha * sc, a2, &tau, &beta, &inv);
+            tau = __shfl_sync(0xffffffffu, tau, 0);
+            beta = __shfl_sync(0xffffffffu, beta, 0) / sc;
+            inv = __shfl_sync(0xffffffffu, inv, 0) * sc;
+            if (tau != 0.0)
+                for (int i = 1 + lane; i < m; i += 32) x[i] = (T)((double)x[i] * inv);
+            __syncwarp();
+            if (lane == 0) {
+                x[0] = (T)beta;
+                *tau_out = (T)tau;
+            }
+            __syncwarp();
+            return tau;
+        }
     }
-    *tau_out = tau;
-    *beta_out = beta;
-    __syncthreads();
+    double tau = 0.0, beta = 0.0, inv = 0.0;
+    if (lane == 0) house_scalars(alpha, ssq, &tau, &beta, &inv);
+    tau = __shfl_sync(0xffffffffu, tau, 0);
+    if (tau != 0.0) {
+        const T invt = (T)__shfl_sync(0xffffffffu, inv, 0);
+        for (int i = 1 + lane; i < m; i += 32) x[i] = x[i] * invt;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        x[0] = (T)beta;
+        *tau_out = (T)tau;
+    }
+    __syncwarp();
+    return tau;
+}
+
+// H = I - tau v v^T applied by one warp to the column segment col[k..m-1]
+// (v[k] = 1 implicit, v[k+1..] stored); two columns at a time for ILP.
+template <typename T>
+__device__ __forceinline__ void warp_apply2(int m, int k, const T *v, T tk, T *c0, T *c1) {
+    const int lane = threadIdx.x & 31;
+    T s0 = 0, s1 = 0;
+    for (int i = k + lane; i < m; i += 32) {
+        const T vi = (i == k) ? T(1) : v[i];
+        s0 += vi * c0[i];
+        if (c1) s1 += vi * c1[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    s0 *= tk;
+    s1 *= tk;
+    for (int i = k + lane; i < m; i += 32) {
+        const T vi = (i == k) ? T(1) : v[i];
+        c0[i] -= s0 * vi;
+        if (c1) c1[i] -= s1 * vi;
+    }
+    __syncwarp();
 }
 
 // Householder QR of the m x nc block P (shared memory, column-major, ld):
-// r = min(nc, m-1) reflectors.  On return R is in the upper trapezoid, the
-// Householder vectors are stored below the diagonal (unit diagonal
-// implicit) and tau[0..r-1] holds the scalars.  Returns r.
+// r = min(nc, m-1) reflectors.  Column c belongs to warp c % nw.  At step k
+// every warp applies H_k to its columns; the owner of column k+1 updates it
+// first and then forms reflector k+1 (lookahead), so each step costs one
+// __syncthreads.  On return R is in the upper trapezoid, the Householder
+// vectors below the diagonal (unit diagonal implicit) and tau[0..r-1] holds
+// the scalars.  Returns r.
 template <typename T>
-__device__ int cta_qr(int m, int nc, T *P, int ld, T *tau, double *red) {
+__device__ int cta_qr(int m, int nc, T *P, int ld, T *tau, double * /*unused*/) {
     const int r = nc < m - 1 ? nc : m - 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k < r; ++k) {
-        double tk, bk;
-        cta_house(m - k, &P[k + (size_t)k * ld], red, &tk, &bk);
-        const T tkt = (T)tk;
-        if (tk != 0.0) {
-            for (int c = k + 1 + warp; c < nc; c += nw) {
-                T *col = &P[(size_t)c * ld];
-                const T *v = &P[(size_t)k * ld];
-                T s = 0;
-                for (int i = k + lane; i < m; i += 32) s += (i == k ? col[i] : v[i] * col[i]);
-                s = warp_sum(s) * tkt;
-                for (int i = k + lane; i < m; i += 32) col[i] -= (i == k ? s : s * v[i]);
-            }
-        }
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (r <= 0) {
         __syncthreads();
-        if (threadIdx.x == 0) {
-            P[k + (size_t)k * ld] = (T)bk;
-            tau[k] = tkt;
+        return r < 0 ? 0 : r;
+    }
+    if (warp == 0) warp_house(m, P, &tau[0]);
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        const T tk = tau[k];
+        const T *v = P + (size_t)k * ld;
+        const int own = (k + 1) % nw;
+        if (warp == own) {
+            if (tk != T(0) && k + 1 < nc) warp_apply2(m, k, v, tk, P + (size_t)(k + 1) * ld, (T *)nullptr);
+            if (k + 1 < r) warp_house(m - k - 1, P + (k + 1) + (size_t)(k + 1) * ld, &tau[k + 1]);
+        }
+        if (tk != T(0)) {
+            int c = k + 2 + ((warp - (k + 2)) % nw + nw) % nw;  // first column > k+1 owned by this warp
+            for (; c < nc; c += 2 * nw) {
+                T *c1 = (c + nw < nc) ? P + (size_t)(c + nw) * ld : (T *)nullptr;
+                warp_apply2(m, k, v, tk, P + (size_t)c * ld, c1);
+            }
         }
         __syncthreads();
     }
@@ -280,19 +414,69 @@ __device__ void cta_extract_u(int m, int r, int rp, const T *P, int ld, T *U, in
 
 // C = alpha * op(A) op(B) + beta * C on shared-memory operands (column-major).
 // op(A) is M x K, op(B) is K x N.  TA: A stored K x M; TB: B stored N x K.
+// Each thread computes a 4 x 4 block of C: rows mb + Mb*i (interleaved, so
+// a warp's A loads hit consecutive addresses) and columns 4*nb + j (a
+// warp's B loads are broadcasts).
 template <typename T, bool TA, bool TB>
 __device__ void cta_gemm(int M, int N, int K, T alpha, const T *A, int lda, const T *B, int ldb, T beta, T *C,
                          int ldc) {
-    for (int idx = threadIdx.x; idx < M * N; idx += blockDim.x) {
-        const int m = idx % M, n = idx / M;
-        T acc = 0;
-        for (int k = 0; k < K; ++k) {
-            const T a = TA ? A[k + (size_t)m * lda] : A[m + (size_t)k * lda];
-            const T b = TB ? B[n + (size_t)k * ldb] : B[k + (size_t)n * ldb];
-            acc += a * b;
+    const int Mb = (M + 3) >> 2, Nb = (N + 3) >> 2;
+    for (int blk = threadIdx.x; blk < Mb * Nb; blk += blockDim.x) {
+        const int mb = blk % Mb, nb = blk / Mb;
+        int mi[4];
+        bool mv[4], nv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            mi[i] = mb + Mb * i;
+            mv[i] = mi[i] < M;
+            if (!mv[i]) mi[i] = M - 1;
+            nv[i] = 4 * nb + i < N;
         }
-        T *c = &C[m + (size_t)n * ldc];
-        *c = (beta == T(0)) ? alpha * acc : alpha * acc + beta * *c;
+        T acc[4][4] = {};
+        for (int k = 0; k < K; ++k) {
+            T a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = TA ? A[k + (size_t)mi[i] * lda] : A[mi[i] + (size_t)k * lda];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int n = nv[j] ? 4 * nb + j : N - 1;
+                bb[j] = TB ? B[n + (size_t)k * ldb] : B[k + (size_t)n * ldb];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * bb[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (!mv[i] || !nv[j]) continue;
+                T *c = &C[mi[i] + (size_t)(4 * nb + j) * ldc];
+                *c = (beta == T(0)) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
+            }
+    }
+}
+
+// --------------------------------------------------- batched global copies
+// Copy `count` elements, element k read by src(k) (a global load) and written
+// by dst(k, v), with U independent loads in flight per thread before any of
+// them is stored: a plain load-then-store loop would wait one full memory
+// latency per element.  Threads [t0, t0 + nt) of the block take part.
+template <typename T, int U = 8, typename Src, typename Dst>
+__device__ __forceinline__ void batched_copy(int count, int t, int nt, Src src, Dst dst) {
+    for (int base = t; base < count; base += U * nt) {
+        T v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = base + u * nt;
+            v[u] = k < count ? src(k) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = base + u * nt;
+            if (k < count) dst(k, v[u]);
+        }
     }
 }
 
@@ -319,6 +503,12 @@ int launch_band_to_band(sev_ctx *h, int n, T *AB, int ldab, int b, int hh, void 
 size_t band_workspace(int n, int b, int hh);
 template <typename T>
 size_t band_smem_bytes(int b, int hh);
+
+// band_tri.cu: b -> 1 in one stage for b in {2, 4, 8, 16, 32}
+int band_tri_supported(int b, int elem);
+size_t band_tri_workspace(int n);
+template <typename T>
+int launch_band_tri(sev_ctx *h, int n, T *AB, int ldab, int b, void *ws, size_t ws_bytes);
 
 // panel.cu + update.cu
 template <typename T>

@@ -92,10 +92,9 @@ __global__ void __launch_bounds__(kThreads)
     T *S = (T *)smem;
     T *tl = S + (size_t)ld * b;
     double *red = (double *)(((uintptr_t)(tl + b) + 15) & ~(uintptr_t)15);
-    for (int idx = threadIdx.x; idx < rows * b; idx += blockDim.x) {
-        const int r = idx % rows, c = idx / rows;
-        S[r + (size_t)c * ld] = P[(size_t)(row0 + r) + (size_t)c * ldp];
-    }
+    batched_copy<T>(
+        rows * b, threadIdx.x, blockDim.x, [&](int k) { return P[(size_t)(row0 + k % rows) + (size_t)(k / rows) * ldp]; },
+        [&](int k, T v) { S[k % rows + (size_t)(k / rows) * ld] = v; });
     __syncthreads();
     const int r = cta_qr(rows, b, S, ld, tl, red);
     for (int idx = threadIdx.x; idx < rows * b; idx += blockDim.x) {
@@ -135,11 +134,13 @@ __global__ void __launch_bounds__(kThreads)
     T *S = (T *)smem;
     T *tl = S + (size_t)ld * b;
     double *red = (double *)(((uintptr_t)(tl + b) + 15) & ~(uintptr_t)15);
-    for (int idx = threadIdx.x; idx < rows * b; idx += blockDim.x) {
-        const int r = idx % rows, c = idx / rows;
-        const int k = r / b, rr = r % b;
-        S[r + (size_t)c * ld] = Rbuf[(size_t)(off_child + c0 + k) * b * b + rr + (size_t)c * b];
-    }
+    batched_copy<T>(
+        rows * b, threadIdx.x, blockDim.x,
+        [&](int k) {
+            const int r = k % rows, c = k / rows;
+            return Rbuf[(size_t)(off_child + c0 + r / b) * b * b + r % b + (size_t)c * b];
+        },
+        [&](int k, T v) { S[k % rows + (size_t)(k / rows) * ld] = v; });
     __syncthreads();
     const int r = cta_qr(rows, b, S, ld, tl, red);
     T *Y = Ynode + (size_t)p * ynode_stride;
@@ -162,16 +163,13 @@ __global__ void __launch_bounds__(kThreads)
 // stored explicitly in Y (shared, rows x b, ld) and tau.
 template <typename T>
 __device__ void cta_apply_reflectors(int rows, int w, int nr, const T *Y, int ld, const T *tl, T *M) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = nr - 1; k >= 0; --k) {
         const T *v = Y + (size_t)k * ld;
         const T tk = tl[k];
-        for (int c = warp; c < w; c += nw) {
-            T *col = M + (size_t)c * ld;
-            T s = 0;
-            for (int i = k + lane; i < rows; i += 32) s += v[i] * col[i];
-            s = warp_sum(s) * tk;
-            for (int i = k + lane; i < rows; i += 32) col[i] -= s * v[i];
+        for (int c = warp; c < w; c += 2 * nw) {
+            T *c1 = (c + nw < w) ? M + (size_t)(c + nw) * ld : (T *)nullptr;
+            warp_apply2(rows, k, v, tk, M + (size_t)c * ld, c1);
         }
         __syncthreads();
     }
@@ -198,18 +196,20 @@ __global__ void __launch_bounds__(kThreads)
     T *Ms = Ys + (size_t)ld * b;
     T *tl = Ms + (size_t)ld * w;
     const int nr = nref[node];
-    for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
-        const int r = idx % rows, c = idx / rows;
-        T z = 0;
-        if (r < b) z = root_identity ? T(r == col0 + c ? 1 : 0) : Zn[r + (size_t)(col0 + c) * b];
-        Ms[r + (size_t)c * ld] = z;
-    }
+    batched_copy<T>(
+        rows * w, threadIdx.x, blockDim.x,
+        [&](int k) {
+            const int r = k % rows, c = k / rows;
+            T z = 0;
+            if (r < b) z = root_identity ? T(r == col0 + c ? 1 : 0) : Zn[r + (size_t)(col0 + c) * b];
+            return z;
+        },
+        [&](int k, T v) { Ms[k % rows + (size_t)(k / rows) * ld] = v; });
     if (nr > 0) {
         const T *Y = Ynode + (size_t)p * ynode_stride;
-        for (int idx = threadIdx.x; idx < rows * nr; idx += blockDim.x) {
-            const int r = idx % rows, c = idx / rows;
-            Ys[r + (size_t)c * ld] = Y[r + (size_t)c * rows];
-        }
+        batched_copy<T>(
+            rows * nr, threadIdx.x, blockDim.x, [&](int k) { return Y[k]; },
+            [&](int k, T v) { Ys[k % rows + (size_t)(k / rows) * ld] = v; });
         for (int c = threadIdx.x; c < nr; c += blockDim.x) tl[c] = tau[(size_t)node * b + c];
     }
     __syncthreads();
@@ -238,14 +238,17 @@ __global__ void __launch_bounds__(kThreads)
     T *tl = Ms + (size_t)ld * w;
     const int nr = nref[l];
     const T *Zl = Zbuf + (size_t)l * b * b;
-    for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
-        const int r = idx % rows, c = idx / rows;
-        Ms[r + (size_t)c * ld] = r < b ? Zl[r + (size_t)(col0 + c) * b] : T(0);
-    }
-    for (int idx = threadIdx.x; idx < rows * nr; idx += blockDim.x) {
-        const int r = idx % rows, c = idx / rows;
-        Ys[r + (size_t)c * ld] = Yleaf[(size_t)(row0 + r) + (size_t)c * ldy];
-    }
+    batched_copy<T>(
+        rows * w, threadIdx.x, blockDim.x,
+        [&](int k) {
+            const int r = k % rows, c = k / rows;
+            return r < b ? Zl[r + (size_t)(col0 + c) * b] : T(0);
+        },
+        [&](int k, T v) { Ms[k % rows + (size_t)(k / rows) * ld] = v; });
+    batched_copy<T>(
+        rows * nr, threadIdx.x, blockDim.x,
+        [&](int k) { return Yleaf[(size_t)(row0 + k % rows) + (size_t)(k / rows) * ldy]; },
+        [&](int k, T v) { Ys[k % rows + (size_t)(k / rows) * ld] = v; });
     for (int c = threadIdx.x; c < nr; c += blockDim.x) tl[c] = tau[(size_t)l * b + c];
     __syncthreads();
     cta_apply_reflectors(rows, w, nr, Ys, ld, tl, Ms);
@@ -268,10 +271,9 @@ __global__ void __launch_bounds__(kThreads)
     T *M = (T *)smem;                 // LU in place: U1 strictly lower, W1 upper
     T *Inv = M + (size_t)ld * b;      // W1^{-1}, then U1^{-1}
     T *Sg = Inv + (size_t)ld * b;     // signs
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-        const int i = idx % b, c = idx / b;
-        M[i + (size_t)c * ld] = Q[i + (size_t)c * ldq];
-    }
+    batched_copy<T>(
+        b * b, threadIdx.x, blockDim.x, [&](int k) { return Q[k % b + (size_t)(k / b) * ldq]; },
+        [&](int k, T v) { M[k % b + (size_t)(k / b) * ld] = v; });
     __syncthreads();
     for (int k = 0; k < b; ++k) {
         if (threadIdx.x == 0) {
@@ -281,8 +283,8 @@ __global__ void __launch_bounds__(kThreads)
             M[k + (size_t)k * ld] = v - s;
         }
         __syncthreads();
-        const T piv = M[k + (size_t)k * ld];
-        for (int i = k + 1 + threadIdx.x; i < b; i += blockDim.x) M[i + (size_t)k * ld] /= piv;
+        const T rpiv = T(1) / M[k + (size_t)k * ld];  // |pivot| >= 1 by the choice of S
+        for (int i = k + 1 + threadIdx.x; i < b; i += blockDim.x) M[i + (size_t)k * ld] *= rpiv;
         __syncthreads();
         const int m = b - k - 1;
         for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
@@ -347,7 +349,9 @@ __global__ void __launch_bounds__(kThreads)
     extern __shared__ __align__(16) unsigned char smem[];
     const int ld = b + 1;
     T *Wi = (T *)smem;
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) Wi[idx % b + (size_t)(idx / b) * ld] = Winv[idx];
+    batched_copy<T>(
+        b * b, threadIdx.x, blockDim.x, [&](int k) { return Winv[k]; },
+        [&](int k, T v) { Wi[k % b + (size_t)(k / b) * ld] = v; });
     __syncthreads();
     const int rows_per = 64;
     const int r0 = b + blockIdx.x * rows_per;
