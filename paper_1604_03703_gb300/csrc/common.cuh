@@ -307,39 +307,53 @@ __device__ double warp_house(int m, T *x, T *tau_out) {
     return tau;
 }
 
-// H = I - tau v v^T applied by one warp to the column segment col[k..m-1]
-// (v[k] = 1 implicit, v[k+1..] stored); two columns at a time for ILP.
+// H = I - tau v v^T applied by one warp to up to four column segments
+// col[k..m-1] (v[k] = 1 implicit, v[k+1..] stored); the four dot products
+// are reduced together so their shuffle chains overlap.
 template <typename T>
-__device__ __forceinline__ void warp_apply2(int m, int k, const T *v, T tk, T *c0, T *c1) {
+__device__ __forceinline__ void warp_apply4(int m, int k, const T *v, T tk, T *c0, T *c1, T *c2, T *c3) {
     const int lane = threadIdx.x & 31;
-    T s0 = 0, s1 = 0;
+    T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
     for (int i = k + lane; i < m; i += 32) {
         const T vi = (i == k) ? T(1) : v[i];
         s0 += vi * c0[i];
         if (c1) s1 += vi * c1[i];
+        if (c2) s2 += vi * c2[i];
+        if (c3) s3 += vi * c3[i];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         s0 += __shfl_xor_sync(0xffffffffu, s0, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
     }
     s0 *= tk;
     s1 *= tk;
+    s2 *= tk;
+    s3 *= tk;
     for (int i = k + lane; i < m; i += 32) {
         const T vi = (i == k) ? T(1) : v[i];
         c0[i] -= s0 * vi;
         if (c1) c1[i] -= s1 * vi;
+        if (c2) c2[i] -= s2 * vi;
+        if (c3) c3[i] -= s3 * vi;
     }
     __syncwarp();
 }
+template <typename T>
+__device__ __forceinline__ void warp_apply2(int m, int k, const T *v, T tk, T *c0, T *c1) {
+    warp_apply4(m, k, v, tk, c0, c1, (T *)nullptr, (T *)nullptr);
+}
 
 // Householder QR of the m x nc block P (shared memory, column-major, ld):
-// r = min(nc, m-1) reflectors.  Column c belongs to warp c % nw.  At step k
-// every warp applies H_k to its columns; the owner of column k+1 updates it
-// first and then forms reflector k+1 (lookahead), so each step costs one
-// __syncthreads.  On return R is in the upper trapezoid, the Householder
-// vectors below the diagonal (unit diagonal implicit) and tau[0..r-1] holds
-// the scalars.  Returns r.
+// r = min(nc, m-1) reflectors.  At step k the warp `own` = (k+1) mod nw
+// applies H_k to column k+1 and forms reflector k+1 (lookahead) -- and
+// nothing else, so the reflector's FP64 chain is the whole of its work --
+// while the other warps apply H_k to columns k+2.. , four at a time.  One
+// __syncthreads per step.  On return R is in the upper trapezoid, the
+// Householder vectors below the diagonal (unit diagonal implicit) and
+// tau[0..r-1] holds the scalars.  Returns r.
 template <typename T>
 __device__ int cta_qr(int m, int nc, T *P, int ld, T *tau, double * /*unused*/) {
     const int r = nc < m - 1 ? nc : m - 1;
@@ -357,12 +371,15 @@ __device__ int cta_qr(int m, int nc, T *P, int ld, T *tau, double * /*unused*/) 
         if (warp == own) {
             if (tk != T(0) && k + 1 < nc) warp_apply2(m, k, v, tk, P + (size_t)(k + 1) * ld, (T *)nullptr);
             if (k + 1 < r) warp_house(m - k - 1, P + (k + 1) + (size_t)(k + 1) * ld, &tau[k + 1]);
-        }
-        if (tk != T(0)) {
-            int c = k + 2 + ((warp - (k + 2)) % nw + nw) % nw;  // first column > k+1 owned by this warp
-            for (; c < nc; c += 2 * nw) {
-                T *c1 = (c + nw < nc) ? P + (size_t)(c + nw) * ld : (T *)nullptr;
-                warp_apply2(m, k, v, tk, P + (size_t)c * ld, c1);
+        } else if (tk != T(0)) {
+            // the other nw - 1 warps share columns k+2 .. nc-1
+            const int q = nw - 1;
+            const int widx = (warp - own - 1 + nw) % nw;
+            for (int c = k + 2 + widx; c < nc; c += 4 * q) {
+                T *c1 = (c + q < nc) ? P + (size_t)(c + q) * ld : (T *)nullptr;
+                T *c2 = (c + 2 * q < nc) ? P + (size_t)(c + 2 * q) * ld : (T *)nullptr;
+                T *c3 = (c + 3 * q < nc) ? P + (size_t)(c + 3 * q) * ld : (T *)nullptr;
+                warp_apply4(m, k, v, tk, P + (size_t)c * ld, c1, c2, c3);
             }
         }
         __syncthreads();

@@ -167,9 +167,11 @@ __device__ void cta_apply_reflectors(int rows, int w, int nr, const T *Y, int ld
     for (int k = nr - 1; k >= 0; --k) {
         const T *v = Y + (size_t)k * ld;
         const T tk = tl[k];
-        for (int c = warp; c < w; c += 2 * nw) {
+        for (int c = warp; c < w; c += 4 * nw) {
             T *c1 = (c + nw < w) ? M + (size_t)(c + nw) * ld : (T *)nullptr;
-            warp_apply2(rows, k, v, tk, M + (size_t)c * ld, c1);
+            T *c2 = (c + 2 * nw < w) ? M + (size_t)(c + 2 * nw) * ld : (T *)nullptr;
+            T *c3 = (c + 3 * nw < w) ? M + (size_t)(c + 3 * nw) * ld : (T *)nullptr;
+            warp_apply4(rows, k, v, tk, M + (size_t)c * ld, c1, c2, c3);
         }
         __syncthreads();
     }

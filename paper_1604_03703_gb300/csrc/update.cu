@@ -308,8 +308,9 @@ int launch_full_to_band(sev_ctx *h, int n, T *A, int lda, int b, T *AB, int ldab
         int rc = panel_factor<T>(h, N, b, P, lda, B.U, B.Tm, B.panel_ws);
         if (rc) return rc;
         const bool tc = tc_update_supported<T>(h, N, b);
+        const bool tc_symm_ok = false;  // the symmetric product still runs on the SIMT tiles
         // Y = A22 U
-        if (tc) {
+        if (tc_symm_ok) {
             rc = tc_symm<T>(h, N, b, A22, lda, B.U, B.Y, B.tc_ws);
             if (rc) return rc;
         } else {
