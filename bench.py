@@ -5,8 +5,8 @@ Workload (default): n = 16384, mixed precision (FP32 data, tensor-core
 trailing update, FP64 Householder norms/tau/beta and FP64 Sturm recurrence),
 A = Q diag(D) Q^T with D geometrically spaced over 1e-6..1 in magnitude with
 random signs and 16-fold clusters of gap 1e-10, Q from the QR of a seeded
-N(0,1) matrix; first half-bandwidth b0 = 128, halvings 128 -> ... -> 1.
-A step is one sev_eigvalsh call (full-to-band, every band halving,
+N(0,1) matrix; first half-bandwidth b0 = 128, band schedule 128 -> 32 -> 1.
+A step is one sev_eigvalsh call (full-to-band, every band-to-band stage,
 bisection).  The FP64 form of the same matrix is timed beside it.
 
 Output: one JSON line on rank 0 (see the keys below).  --impl reference
@@ -132,30 +132,61 @@ def panel_sizes(n, b):
     return out
 
 
-def schedule(b0):
+def schedule(b0, elem=4):
+    """The library's band schedule: straight to 1 from b <= 32 (b <= 16 for
+    FP64), a wider band first to the widest such width dividing it."""
+    def tri(b):
+        return b in (2, 4, 8, 16) or (b == 32 and elem == 4)
     s = [b0]
     while s[-1] > 1:
         b = s[-1]
-        s.append(b // 2 if b % 2 == 0 else 1)
+        nxt = 1 if b % 2 else b // 2
+        if tri(b):
+            nxt = 1
+        else:
+            w = 32
+            while w >= 2:
+                if tri(w) and b % w == 0 and w < b:
+                    nxt = w
+                    break
+                w //= 2
+        s.append(nxt)
     return s
 
 
 def kernel_model(name, n, b0, elem):
-    """Algorithmic work of one step for a kernel: (amount, unit, bound)."""
+    """Algorithmic work of one step for a kernel: (amount, unit, bound).
+
+    syr2k / symm: 2 N^2 b flops per panel (lower triangle, both products).
+    band stages b -> h (k = b/h): each of the n/h sweeps reads and writes the
+    2b stored diagonals of the columns it passes, ~2 s 2b (n - ih) bytes, so
+    2 s k n^2 bytes per stage; the b -> 1 stage is k = b.
+    tree-QR nodes: 2(2b)b^2 - (2/3)b^3 flops per stacked-triangle QR.
+    bisection: n eigenvalues x iterations x n Sturm steps (one FP64 divide each).
+    """
     Ns = panel_sizes(n, b0)
+    sched = schedule(b0, elem)
     if name in ("syr2k", "syr2k_tc"):
         flops = sum(2.0 * N * (N + 1) * b0 for N in Ns)
         return flops, "flop", "tensor" if name.endswith("_tc") else "alu"
     if name in ("symm", "symm_tc"):
         flops = sum(2.0 * N * N * b0 for N in Ns)
         return flops, "flop", "tensor" if name.endswith("_tc") else "alu"
+    if name == "band_tri":
+        b1 = sched[-2]
+        return 2.0 * elem * b1 * float(n) ** 2, "byte", "hbm"
     if name == "band_chase":
-        # one read + one write of the active band per sweep (k = 2 halvings):
-        # 2 k s n^2 bytes per stage
-        stages = len(schedule(b0)) - 1
-        return stages * 2 * 2 * elem * float(n) ** 2, "byte", "hbm"
+        tot = 0.0
+        for b, h in zip(sched[:-1], sched[1:]):
+            if h == 1 and (b in (2, 4, 8, 16) or (b == 32 and elem == 4)):
+                continue
+            tot += 2.0 * elem * (b // h) * float(n) ** 2
+        return tot, "byte", "hbm"
+    if name == "tsqr_node_qr":
+        r_leaf = 128 if b0 >= 64 else 256
+        nodes = sum(max(N // r_leaf - 1, 0) for N in Ns)
+        return nodes * (4.0 * b0 ** 3 - 2.0 * b0 ** 3 / 3.0), "flop", "alu"
     if name == "bisect":
-        # Sturm steps (one FP64 division each): n eigenvalues x ~iterations x n
         rtol = 1e-9 if elem == 4 else 1e-14
         iters = math.ceil(math.log2(2.0 / rtol)) + 1
         return float(n) * n * iters, "sturm_step", "alu"
@@ -423,8 +454,8 @@ def run_ours(args):
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+bf16x3 (f64 norms, f64 Sturm)", "data": "synthetic",
         "config": {"workload": "eigvalsh n=%d, A = Q diag(D) Q^T, D geometric 1e-6..1 with random signs and "
-                               "16-fold clusters (gap 1e-10), FP32 data, b0=%d halving to 1" % (n, b0),
-                   "n": n, "b0": b0, "parallelism": "replicas" if world > 1 else "single",
+                               "16-fold clusters (gap 1e-10), FP32 data, bands %s" % (n, "->".join(map(str, schedule(b0, 4)))),
+                   "n": n, "b0": b0, "schedule": schedule(b0, 4), "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (1 GiB matrix per step); input restore excluded from step events"},
         "max_err_vs_D": err,
         "e2e": e2e,

@@ -90,16 +90,28 @@ static int default_b0(int n, int prec) {
     return n >= 12288 ? 128 : (n >= 1024 ? 64 : 32);
 }
 
-// Band schedule (Algorithm 4.3 with k = 2 halvings): b0 -> b0/2 -> ...
-// until b <= 32 is a power of two, which then goes to 1 in one stage (k = b,
-// the larger reduction factor the paper allows per stage); an odd b also
-// finishes with b -> 1.
+// Band schedule (Algorithm 4.3; the paper allows a reduction factor k > 2
+// per stage): a band the one-stage b -> 1 kernel supports goes straight to 1;
+// a wider band first goes to the widest such width that divides it (one
+// stage with k = b/32 for b0 = 128 -- the measured best on this part, since a
+// stage's critical path is ~3n/h chases of ~h reflector steps each) or, when
+// none divides it, is halved; an odd band finishes with b -> 1.
 static int schedule(int b0, int elem, int *out) {
     int k = 0;
     out[k++] = b0;
     while (out[k - 1] > 1) {
         const int b = out[k - 1];
-        out[k++] = (band_tri_supported(b, elem) || b % 2 != 0) ? 1 : b / 2;
+        int next = b % 2 != 0 ? 1 : b / 2;
+        if (band_tri_supported(b, elem)) {
+            next = 1;
+        } else {
+            for (int w = 32; w >= 2; w >>= 1)
+                if (band_tri_supported(w, elem) && b % w == 0 && w < b) {
+                    next = w;
+                    break;
+                }
+        }
+        out[k++] = next;
     }
     return k;
 }

@@ -25,6 +25,21 @@
 // the kernel latches SEV_ERR_TIMEOUT and returns.
 #include "common.cuh"
 
+#ifdef SEV_TRACE
+static __device__ long long *sev_btrace = nullptr;
+extern "C" int sev_trace_set_band(void *p) {
+    return cudaMemcpyToSymbol(sev_btrace, &p, sizeof(p)) == cudaSuccess ? 0 : 1;
+}
+#define BTRACE(k)                                                              \
+    do {                                                                       \
+        if (threadIdx.x == 0 && sev_btrace && i == 40 && j == 20) sev_btrace[k] = clock64(); \
+    } while (0)
+#else
+#define BTRACE(k) \
+    do {          \
+    } while (0)
+#endif
+
 namespace sev {
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -125,12 +140,15 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     const int ldb1 = S.ldb1, ldh1 = S.ldh1;
     const int tid = threadIdx.x, nt = blockDim.x;
 
+    BTRACE(0);
     // 1. QR of the n_r x h block
     batched_copy<T>(
         n_r * h, tid, nt, [&](int k) { return bld(AB, ldab, n, o_qr_r + k % n_r, o_qr_c + k / n_r, bad); },
         [&](int k, T v) { S.Xs[k % n_r + (size_t)(k / n_r) * ldb1] = v; });
     __syncthreads();
+    BTRACE(1);
     const int nr = cta_qr(n_r, h, S.Xs, ldb1, S.tau, S.red);
+    BTRACE(2);
     // 2. B[qr rows, qr cols] = [R; 0]
     for (int idx = tid; idx < n_r * h; idx += nt) {
         const int r = idx % n_r, c = idx / n_r;
@@ -146,6 +164,7 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     cta_form_t(n_r, nr, S.Xs, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
     cta_gemm<T, false, false>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, T(0), S.UTs, ldb1);
     __syncthreads();
+    BTRACE(3);
     // 4. the qr-row diagonal block X_d (n_r x n_r): two-sided update
     batched_copy<T>(
         n_r * n_r, tid, nt, [&](int k) { return bld_sym(AB, ldab, n, o_qr_r + k % n_r, o_qr_r + k / n_r, bad); },
@@ -180,6 +199,7 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
     }
     __syncthreads();
+    BTRACE(4);
     // 5. the other rows of W (above: [0, o_v), below: [o_v + n_r, n_c)):
     //    X <- X - (X U T) U^T, in chunks of at most b rows
     for (int part = 0; part < 2; ++part) {
@@ -203,6 +223,7 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
             __syncthreads();
         }
     }
+    BTRACE(5);
 }
 
 template <typename T>
@@ -239,7 +260,6 @@ __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int 
                             s_abort = 1;
                             break;
                         }
-                        __nanosleep(128);
                     }
                 }
                 __syncthreads();
@@ -247,10 +267,9 @@ __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int 
             }
             band_chase(AB, ldab, n, b, h, i, j, S, &s_bad);
             __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                st_release(&progress[s], j);
-            }
+            // the release store orders the CTA's writes (made visible to
+            // thread 0 by the barrier above) before the progress flag
+            if (threadIdx.x == 0) st_release(&progress[s], j);
         }
     }
     __syncthreads();

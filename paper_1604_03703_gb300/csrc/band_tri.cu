@@ -338,7 +338,6 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                     int pv = 0;
                     if (lane == 0) {
                         const long long t0 = clock64();
-                        unsigned ns = 32;
                         while ((pv = ld_acquire_i(&progress[gi - 1])) < need) {
                             if (*(volatile int *)err != 0 || s_abort) {
                                 pv = -1;
@@ -349,8 +348,7 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                                 pv = -1;
                                 break;
                             }
-                            __nanosleep(ns);
-                            if (ns < 512) ns <<= 1;
+
                         }
                     }
                     pv = __shfl_sync(0xffffffffu, pv, 0);

@@ -135,8 +135,17 @@ def qdq_torch(D, seed: int, device, dtype=None):
     """A = Q diag(D) Q^T generated with torch on ``device`` in FP64 (for the
     n = 16384 workload, whose host QR would take minutes).  Same recipe as
     ``qdq``; the random stream is torch's, seeded with ``seed``."""
+    import ctypes
+    import os
+
     import torch
 
+    if torch.device(device).type == "cuda":
+        # Load torch's CUDA linear-algebra library by full path first: under a
+        # profiler's injected environment its lazy dlopen by bare name can miss.
+        lib = os.path.join(os.path.dirname(torch.__file__), "lib", "libtorch_cuda_linalg.so")
+        if os.path.exists(lib):
+            ctypes.CDLL(lib, mode=ctypes.RTLD_GLOBAL)
     g = torch.Generator(device=device)
     g.manual_seed(seed)
     n = len(D)
