@@ -69,6 +69,8 @@ def _load():
             lib.orc_jacobi.argtypes = [i, _dp, i, _dp]
             lib.orc_inertia.restype = i
             lib.orc_inertia.argtypes = [i, _dp, i, d]
+            lib.orc_band_inertia.restype = i
+            lib.orc_band_inertia.argtypes = [i, _dp, i, i, d]
             lib.orc_panel_qr.restype = i
             lib.orc_panel_qr.argtypes = [i, i, _dp, i, _dp, i, _dp, i]
             lib.orc_full_to_band.restype = None
@@ -189,6 +191,39 @@ def inertia(A, x: float) -> int:
     """Number of eigenvalues of A below x via long-double LDL^T of A - xI."""
     M = _fortran(A)
     return _load().orc_inertia(M.shape[0], _ptr(M), M.shape[0], float(x))
+
+
+def band_inertia(AB, b: int, x: float) -> int:
+    """Number of eigenvalues below x of the symmetric band matrix held in
+    packed lower storage AB (ldab x n, AB[d, j] = B[j + d, j]), by banded
+    LDL^T of B - xI (Sylvester), O(n b^2)."""
+    AB = np.asfortranarray(np.asarray(AB, dtype=np.float64))
+    ldab, n = AB.shape
+    return _load().orc_band_inertia(n, _ptr(AB), ldab, int(b), float(x))
+
+
+def inertia_lapack(A, x: float) -> int:
+    """Number of eigenvalues of the symmetric A (lower triangle read) below
+    x by Sylvester's law of inertia, with LAPACK's Bunch-Kaufman LDL^T
+    (scipy.linalg.ldl) as the factorisation step: the count of negative
+    eigenvalues of its block-diagonal D (1x1 and 2x2 blocks).  For dense
+    matrices too large for the long-double factorisation above."""
+    import scipy.linalg
+
+    M = np.array(A, dtype=np.float64, order="F", copy=True)
+    M[np.diag_indices_from(M)] -= x
+    _, Dm, _ = scipy.linalg.ldl(M, lower=True, overwrite_a=True, check_finite=False)
+    neg, i, n = 0, 0, Dm.shape[0]
+    while i < n:
+        if i + 1 < n and Dm[i + 1, i] != 0.0:
+            a, c, bb = Dm[i, i], Dm[i + 1, i + 1], Dm[i + 1, i]
+            det = a * c - bb * bb
+            neg += 1 if det < 0 else (2 if a + c < 0 else 0)
+            i += 2
+        else:
+            neg += Dm[i, i] < 0
+            i += 1
+    return int(neg)
 
 
 # ------------------------------------------------------------- stage oracles

@@ -24,6 +24,7 @@
  *   orc_eigvalsh         orc_tridiagonalize + orc_bisect (Algorithm 4.3's result)
  *   orc_jacobi           cyclic Jacobi (independent cross-check, n <= ~32)
  *   orc_inertia          LDL^T inertia of A - xI in long double (Sylvester)
+ *   orc_band_inertia     the same for a packed band matrix, O(n b^2)
  *   orc_panel_qr         Householder QR of a panel + forward compact-WY T
  *   orc_full_to_band     Algorithm 4.1, right-looking, with the Eq. 4.1 update
  *   orc_band_to_band     Algorithm 4.2 on dense storage, with the readings
@@ -346,6 +347,45 @@ int orc_inertia(int n, const double *A, int lda, double x)
         for (int i = k + 1; i < n; ++i) L[IDX(i, k, n)] /= piv;
     }
     free(L);
+    return neg;
+}
+
+/*
+ * Number of eigenvalues of a banded symmetric B strictly below x: the
+ * negative pivots of the unpivoted LDL^T factorisation of B - xI
+ * (Sylvester's law of inertia), in long double.  B is given in packed lower
+ * band storage AB[d + j*ldab] = B(j+d, j), 0 <= d <= b.  Without pivoting
+ * the factor L keeps the half-bandwidth b, so the work is O(n b^2): this is
+ * what checks eigenvalue counts of band matrices too large for a full
+ * eigensolve.  A pivot of magnitude below DBL_MIN is replaced by -DBL_MIN
+ * (the Sturm-count convention).
+ */
+int orc_band_inertia(int n, const double *AB, int ldab, int b, double x)
+{
+    const size_t ldl = (size_t)b + 1;
+    long double *L = (long double *)calloc(ldl * (size_t)n, sizeof(long double));
+    long double *D = (long double *)malloc(sizeof(long double) * (size_t)n);
+    int neg = 0;
+    for (int j = 0; j < n; ++j) {
+        int k0 = j - b > 0 ? j - b : 0;
+        long double s = (long double)AB[(size_t)j * ldab] - (long double)x;
+        for (int k = k0; k < j; ++k) {
+            long double l = L[(size_t)(j - k) + (size_t)k * ldl];
+            s -= l * l * D[k];
+        }
+        if (fabsl(s) < (long double)DBL_MIN) s = -(long double)DBL_MIN;
+        D[j] = s;
+        if (s < 0.0L) ++neg;
+        for (int i = j + 1; i <= j + b && i < n; ++i) {
+            long double t = (long double)AB[(size_t)(i - j) + (size_t)j * ldab];
+            int ki = i - b > 0 ? i - b : 0;
+            for (int k = ki; k < j; ++k)
+                t -= L[(size_t)(i - k) + (size_t)k * ldl] * L[(size_t)(j - k) + (size_t)k * ldl] * D[k];
+            L[(size_t)(i - j) + (size_t)j * ldl] = t / s;
+        }
+    }
+    free(L);
+    free(D);
     return neg;
 }
 

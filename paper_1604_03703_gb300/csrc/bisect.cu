@@ -142,10 +142,234 @@ __global__ void bisect_kernel(int n, const double *__restrict__ d, const double 
     eigs[k] = __dmul_rn(0.5, __dadd_rn(lo, hi));
 }
 
+// ------------------------------------------------- shared-interval rounds
+// The per-eigenvalue bisection above visits, for index k, the path of
+// intervals that the counts at its midpoints dictate.  Indices whose
+// intervals coincide take identical steps (same midpoint, same count, same
+// stopping test), and by monotonicity of the count they form contiguous
+// runs of k.  bisect_rounds_kernel exploits both facts without changing a
+// single rounding: every round (1) lists the distinct active intervals
+// (leaders), (2) evaluates, for each leader, the counts at all midpoints of
+// its subtree of depth d -- the midpoints its next d bisection steps can
+// reach, computed by the same IEEE operations -- with d as deep as the
+// thread budget allows, and (3) lets every index walk d steps down its
+// leader's subtree using those counts.  The result is bitwise the one of
+// bisect_kernel; the chain of dependent Sturm counts per index shrinks from
+// one per level to one per round (the early levels, where few intervals are
+// distinct, are resolved many at a time).
+//
+// The kernel is persistent and cooperative (all CTAs resident); the three
+// phases of a round are separated by a grid barrier with a capped wait.
+struct BisCtl {
+    int bar;    // monotone arrival counter of the grid barrier
+    int D;      // leaders this round
+    int depth;  // subtree depth this round
+    int done;   // no active index left
+    int abort;  // a wait hit its cap
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier number `seq` (1, 2, ...): returns false if the wait hit its cap
+// or another CTA gave up.
+__device__ bool bis_barrier(BisCtl *ctl, int seq, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(&ctl->bar, 1);
+        const int target = seq * (int)gridDim.x;
+        const long long t0 = clock64();
+        int ok = 1;
+        while (ld_acquire_gpu(&ctl->bar) < target) {
+            if (*(volatile int *)&ctl->abort) {
+                ok = 0;
+                break;
+            }
+            if (wait_expired(t0)) {
+                latch_error(err, SEV_ERR_TIMEOUT);
+                *(volatile int *)&ctl->abort = 1;
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The stopping test of one bisection step on [lo, hi] (same operations and
+// order as bisect_kernel).  Returns 0 to continue with mid, 1 when converged
+// or mid no longer splits, 2 when the step cap is reached.
+__device__ __forceinline__ int bis_step_test(double lo, double hi, int it, double rtol, double atol, int maxit,
+                                             double &mid) {
+    const double w = __dsub_rn(hi, lo);
+    const double mag = fmax(fabs(lo), fabs(hi));
+    double tol = __dmul_rn(rtol, mag);
+    if (atol > tol) tol = atol;
+    if (w <= tol) return 1;
+    if (it >= maxit) return 2;
+    mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
+    if (mid <= lo || mid >= hi) return 1;
+    return 0;
+}
+
+struct BisWs {
+    double *lo, *hi;
+    int *it, *st;        // steps taken; state: 0 active, 1 finished
+    int *lead, *leadof;  // leader list; leader slot of each index
+    int *cnt;            // counts of the round's subtree midpoints
+    BisCtl *ctl;
+};
+
+constexpr int kBisThreads = 256;
+constexpr int kBisMaxItems = 131072;
+
+__global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const double *__restrict__ d,
+                                                                    const double *__restrict__ e2,
+                                                                    const double *__restrict__ par, double rtol,
+                                                                    int maxit, int budget, double *__restrict__ eigs,
+                                                                    BisWs W, int *err) {
+    __shared__ int s_scan[kBisThreads];
+    const double pivmin = par[2];
+    const double atol = __dmul_rn(rtol, par[3]);
+    const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int gthreads = gridDim.x * blockDim.x;
+    for (int k = gtid; k < n; k += gthreads) {
+        W.lo[k] = par[0];
+        W.hi[k] = par[1];
+        W.it[k] = 0;
+        W.st[k] = 0;
+    }
+    int seq = 0;
+    if (!bis_barrier(W.ctl, ++seq, err)) return;
+    for (;;) {
+        // ---- (1) leaders: CTA 0 compacts the distinct active intervals
+        if (blockIdx.x == 0) {
+            const int chunk = (n + kBisThreads - 1) / kBisThreads;
+            const int k0 = threadIdx.x * chunk, k1 = min(n, k0 + chunk);
+            int mine = 0;
+            for (int k = k0; k < k1; ++k)
+                if (W.st[k] == 0 && (k == 0 || W.st[k - 1] != 0 || W.lo[k] != W.lo[k - 1] || W.hi[k] != W.hi[k - 1]))
+                    ++mine;
+            s_scan[threadIdx.x] = mine;
+            __syncthreads();
+            for (int off = 1; off < kBisThreads; off <<= 1) {  // inclusive scan
+                const int v = threadIdx.x >= off ? s_scan[threadIdx.x - off] : 0;
+                __syncthreads();
+                s_scan[threadIdx.x] += v;
+                __syncthreads();
+            }
+            int pos = s_scan[threadIdx.x] - mine;  // leaders before this chunk
+            for (int k = k0; k < k1; ++k) {
+                if (W.st[k] != 0) continue;
+                if (k == 0 || W.st[k - 1] != 0 || W.lo[k] != W.lo[k - 1] || W.hi[k] != W.hi[k - 1]) W.lead[pos++] = k;
+                W.leadof[k] = pos - 1;
+            }
+            if (threadIdx.x == kBisThreads - 1) {
+                // depth: fewest rounds per level, counting a round as one
+                // chain latency while its items fit the budget of chains the
+                // GPU keeps in flight, and proportionally longer beyond it
+                const int D = s_scan[kBisThreads - 1];
+                const long cap = n > kBisMaxItems ? n : kBisMaxItems;
+                int dep = 1;
+                double best = 2.0;
+                for (int t = 1; t <= 24; ++t) {
+                    const long items = (long)D * ((1L << t) - 1);
+                    if (items > cap) break;
+                    const double cost = fmax(1.0, (double)items / (double)budget) / t;
+                    if (cost < best) {
+                        best = cost;
+                        dep = t;
+                    }
+                }
+                W.ctl->D = D;
+                W.ctl->depth = dep;
+                W.ctl->done = D == 0;
+            }
+        }
+        if (!bis_barrier(W.ctl, ++seq, err)) return;
+        if (*(volatile int *)&W.ctl->done) break;
+        const int D = *(volatile int *)&W.ctl->D;
+        const int dep = *(volatile int *)&W.ctl->depth;
+        const int M = (1 << dep) - 1;
+        // ---- (2) counts at every midpoint of every leader's subtree
+        const long items = (long)D * M;
+        // items are dealt round-robin over the CTAs so every SM gets its share
+        for (long w = blockIdx.x + (long)threadIdx.x * gridDim.x; w < items; w += gthreads) {
+            const int j = (int)(w / M), m = (int)(w % M);
+            const int k = W.lead[j];
+            double lo = W.lo[k], hi = W.hi[k], mid = 0.0;
+            int it = W.it[k];
+            // node m in heap order: its depth is floor(log2(m + 1)); the bits of
+            // m + 1 below the leading one, top first, are the turns (1 = right)
+            const int path = m + 1;
+            const int lev = 31 - __clz(path);
+            bool live = true;
+            for (int l = lev - 1; l >= 0 && live; --l) {
+                if (bis_step_test(lo, hi, it, rtol, atol, maxit, mid) != 0) {
+                    live = false;
+                    break;
+                }
+                if ((path >> l) & 1)
+                    lo = mid;
+                else
+                    hi = mid;
+                ++it;
+            }
+            int c = -1;
+            if (live && bis_step_test(lo, hi, it, rtol, atol, maxit, mid) == 0) c = sturm_count(n, d, e2, mid, pivmin);
+            W.cnt[w] = c;
+        }
+        if (!bis_barrier(W.ctl, ++seq, err)) return;
+        // ---- (3) every active index walks dep steps down its leader's subtree
+        for (int k = gtid; k < n; k += gthreads) {
+            if (W.st[k] != 0) continue;
+            const int j = W.leadof[k];
+            double lo = W.lo[k], hi = W.hi[k], mid = 0.0;
+            int it = W.it[k], node = 0, state = 0;
+            for (int l = 0; l < dep; ++l) {
+                const int r = bis_step_test(lo, hi, it, rtol, atol, maxit, mid);
+                if (r != 0) {
+                    state = r;
+                    break;
+                }
+                if (W.cnt[(long)j * M + node] >= k + 1) {
+                    hi = mid;
+                    node = 2 * node + 1;
+                } else {
+                    lo = mid;
+                    node = 2 * node + 2;
+                }
+                ++it;
+            }
+            if (state == 0) state = bis_step_test(lo, hi, it, rtol, atol, maxit, mid);
+            if (state == 2) latch_error(err, SEV_ERR_NOCONV);
+            W.lo[k] = lo;
+            W.hi[k] = hi;
+            W.it[k] = it;
+            W.st[k] = state != 0;
+        }
+        if (!bis_barrier(W.ctl, ++seq, err)) return;
+    }
+    for (int k = gtid; k < n; k += gthreads) eigs[k] = __dmul_rn(0.5, __dadd_rn(W.lo[k], W.hi[k]));
+}
+
 size_t bisect_workspace(int n) {
     Carver c(nullptr);
     c.take<double>((size_t)n + 1);
     c.take<double>(4);
+    c.take<double>((size_t)n);
+    c.take<double>((size_t)n);
+    for (int a = 0; a < 4; ++a) c.take<int>((size_t)n);
+    c.take<int>((size_t)(n > kBisMaxItems ? n : kBisMaxItems));
+    c.take<BisCtl>(1);
     return c.bytes();
 }
 
@@ -156,11 +380,36 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     Carver c(ws);
     double *e2 = c.take<double>((size_t)n + 1);
     double *par = c.take<double>(4);
+    BisWs W;
+    W.lo = c.take<double>((size_t)n);
+    W.hi = c.take<double>((size_t)n);
+    W.it = c.take<int>((size_t)n);
+    W.st = c.take<int>((size_t)n);
+    W.lead = c.take<int>((size_t)n);
+    W.leadof = c.take<int>((size_t)n);
+    W.cnt = c.take<int>((size_t)(n > kBisMaxItems ? n : kBisMaxItems));
+    W.ctl = c.take<BisCtl>(1);
     SEV_LAUNCH(h, K_BISECT_PREP, bisect_prep_kernel, 1, 1024, 0, n, d, e, e2, par);
-    // one thread per eigenvalue; small blocks spread the indices over all SMs
-    int bs = 64;
-    while (bs > 32 && (n + bs - 1) / bs < h->sm_count) bs >>= 1;
-    SEV_LAUNCH(h, K_BISECT, bisect_kernel, (n + bs - 1) / bs, bs, 0, n, d, e2, par, rtol, 200, eigs, h->d_err);
+    if (n == 1) {
+        SEV_CUDA(cudaMemcpyAsync(eigs, d, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+        return SEV_OK;
+    }
+    SEV_CUDA(cudaMemsetAsync(W.ctl, 0, sizeof(BisCtl), h->stream));
+    // one CTA per SM: enough Sturm chains in flight to cover the FP64 divide
+    // latency, and every CTA resident for the grid barrier
+    int per_sm = 0;
+    SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bisect_rounds_kernel, kBisThreads, 0));
+    if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
+    // ~6 warps of Sturm chains per SM keep its FP64 pipe busy through the
+    // latency of a step (about 12 FP64 instructions, ~1000 cycles)
+    const int grid = h->sm_count;
+    int budget = grid * 192;
+    int maxit = 200;
+    void *args[] = {(void *)&n, (void *)&d, (void *)&e2, (void *)&par, (void *)&rtol, (void *)&maxit,
+                    (void *)&budget, (void *)&eigs, (void *)&W, (void *)&h->d_err};
+    timing_begin(h, K_BISECT);
+    SEV_CUDA(cudaLaunchCooperativeKernel((const void *)bisect_rounds_kernel, grid, kBisThreads, args, 0, h->stream));
+    timing_end(h, K_BISECT);
     return SEV_OK;
 }
 

@@ -93,6 +93,18 @@ def random_band(n: int, b: int, seed: int) -> np.ndarray:
     return L + np.tril(L, -1).T
 
 
+def random_band_packed(n: int, b: int, ldab: int, seed: int) -> np.ndarray:
+    """Packed lower band (ldab x n, AB[d, j] = B[j + d, j]) of a symmetric
+    matrix with half-bandwidth b and N(0,1) entries in the band; rows d > b
+    and the entries past the matrix's end are zero."""
+    AB = rng(seed).standard_normal((ldab, n))
+    AB[b + 1:, :] = 0.0
+    for dd in range(1, min(b, n - 1) + 1):
+        AB[dd, n - dd:] = 0.0
+    AB[min(b, n - 1) + 1: b + 1, :] = 0.0
+    return AB
+
+
 def dense_to_band(A: np.ndarray, ldab: int) -> np.ndarray:
     """Packed lower band storage: AB[d, j] = A[j + d, j] for 0 <= d < ldab
     (column-major, i.e. AB is ldab x n with column j contiguous)."""

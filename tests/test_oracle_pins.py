@@ -328,3 +328,41 @@ def test_bisect_range_matches_full(orc):
     d, e = I.random_tridiagonal(90, 12)
     full = orc.bisect(d, e, 1e-14)
     np.testing.assert_array_equal(orc.bisect_range(d, e, 10, 33, 1e-14), full[10:33])
+
+
+@pytest.mark.parametrize("n,b", [(40, 5), (64, 1), (33, 8), (7, 6)])
+def test_band_inertia_counts(orc, n, b):
+    """Sylvester: negative LDL^T pivots of B - xI count the eigenvalues below
+    x; pinned to the eigenvalues of the dense matrix (LAPACK) at shifts in
+    the middle of spectral gaps, and to the tridiagonal Sturm count at b = 1."""
+    AB = I.random_band_packed(n, b, 2 * b + 2, 7100 + n + b)
+    B = I.band_to_dense(AB)
+    lam = np.linalg.eigvalsh(B)
+    xs = [lam[0] - 1.0, lam[-1] + 1.0] + [0.5 * (lam[k] + lam[k + 1]) for k in range(0, n - 1, max(1, n // 7))]
+    for x in xs:
+        want = int((lam < x).sum())
+        assert orc.band_inertia(AB, b, x) == want
+        assert orc.inertia(B, x) == want
+        if b == 1:
+            assert orc.sturm_count(AB[0], AB[1, : n - 1], x) == want
+
+
+def test_band_inertia_diagonal_closed_form(orc):
+    d = np.array([3.0, -1.0, 2.0, -5.0, 0.5])
+    AB = np.zeros((3, 5))
+    AB[0] = d
+    for x in (-6.0, -2.0, 0.0, 1.0, 2.5, 4.0):
+        assert orc.band_inertia(AB, 2, x) == int((d < x).sum())
+
+
+def test_inertia_lapack_counts(orc):
+    """LAPACK Bunch-Kaufman LDL^T as the factorisation step: pinned to
+    eigenvalue counts, including 2x2 pivots (a zero-diagonal matrix)."""
+    A = I.semicircle(60, 77)
+    lam = np.linalg.eigvalsh(A)
+    for x in [lam[0] - 1.0, 0.5 * (lam[9] + lam[10]), 0.5 * (lam[40] + lam[41]), lam[-1] + 1.0]:
+        assert orc.inertia_lapack(A, x) == int((lam < x).sum())
+    K = np.kron(np.eye(5), np.array([[0.0, 1.0], [1.0, 0.0]]))  # eigenvalues +-1, forces 2x2 pivots
+    assert orc.inertia_lapack(K, 0.0) == 5
+    assert orc.inertia_lapack(K, -2.0) == 0
+    assert orc.inertia_lapack(K, 2.0) == 10
