@@ -166,6 +166,8 @@ struct BisCtl {
     int depth;  // subtree depth this round
     int done;   // no active index left
     int abort;  // a wait hit its cap
+    int rounds;       // rounds run (diagnostics)
+    long long items;  // subtree midpoints evaluated (diagnostics)
 };
 
 __device__ __forceinline__ int ld_acquire_gpu(const int *p) {
@@ -220,6 +222,14 @@ __device__ __forceinline__ int bis_step_test(double lo, double hi, int it, doubl
     return 0;
 }
 
+// The count as a separate (not inlined) function: its loop is compiled on
+// its own, as tight as in bisect_kernel, whatever the round logic around it
+// keeps live.
+__device__ __noinline__ int sturm_chain(int n, const double *__restrict__ d, const double *__restrict__ e2, double x,
+                                        double pivmin) {
+    return sturm_count(n, d, e2, x, pivmin);
+}
+
 struct BisWs {
     double *lo, *hi;
     int *it, *st;        // steps taken; state: 0 active, 1 finished
@@ -228,7 +238,7 @@ struct BisWs {
     BisCtl *ctl;
 };
 
-constexpr int kBisThreads = 256;
+constexpr int kBisThreads = 1024;
 constexpr int kBisMaxItems = 131072;
 
 __global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const double *__restrict__ d,
@@ -292,6 +302,10 @@ __global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const
                 W.ctl->D = D;
                 W.ctl->depth = dep;
                 W.ctl->done = D == 0;
+                if (D > 0) {
+                    W.ctl->rounds += 1;
+                    W.ctl->items += (long long)D * ((1L << dep) - 1);
+                }
             }
         }
         if (!bis_barrier(W.ctl, ++seq, err)) return;
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const
                 ++it;
             }
             int c = -1;
-            if (live && bis_step_test(lo, hi, it, rtol, atol, maxit, mid) == 0) c = sturm_count(n, d, e2, mid, pivmin);
+            if (live && bis_step_test(lo, hi, it, rtol, atol, maxit, mid) == 0) c = sturm_chain(n, d, e2, mid, pivmin);
             W.cnt[w] = c;
         }
         if (!bis_barrier(W.ctl, ++seq, err)) return;
@@ -400,10 +414,13 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     int per_sm = 0;
     SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bisect_rounds_kernel, kBisThreads, 0));
     if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
-    // ~6 warps of Sturm chains per SM keep its FP64 pipe busy through the
-    // latency of a step (about 12 FP64 instructions, ~1000 cycles)
+    // A Sturm step is a chain of dependent FP64 operations (~1000 cycles on
+    // GB300); about 146 chains per SM cover that latency with the FP64 pipe
+    // busy (measured: ~44 G steps/s at saturation, 7.7 ms per 16384-step
+    // chain alone).  Rounds are sized to that budget; 1024 threads per CTA
+    // run a round of up to 150K chains in a single pass.
     const int grid = h->sm_count;
-    int budget = grid * 192;
+    int budget = grid * 146;
     int maxit = 200;
     void *args[] = {(void *)&n, (void *)&d, (void *)&e2, (void *)&par, (void *)&rtol, (void *)&maxit,
                     (void *)&budget, (void *)&eigs, (void *)&W, (void *)&h->d_err};
