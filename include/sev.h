@@ -9,8 +9,8 @@
  *   full-to-band    Algorithm 4.1 (tree QR of each panel, Algorithm 3.2;
  *                   compact-WY by Householder reconstruction, Cor. 3.7;
  *                   two-sided trailing update, Eq. 4.1)
- *   band-to-band    Algorithm 4.2 (bulge chasing, b -> h), repeated
- *                   b0 -> b0/2 -> ... -> 1 as in Algorithm 4.3
+ *   band-to-band    Algorithm 4.2 (bulge chasing, b -> h), repeated down
+ *                   to the tridiagonal as in Algorithm 4.3
  *   tridiag_bisect  eigenvalues of the final tridiagonal by Sturm-count
  *                   bisection (the "compute its eigenvalues" step of
  *                   Algorithm 4.3)
@@ -89,7 +89,9 @@ int sev_set_workspace(sev_handle handle, void *workspace, size_t bytes);
 
 /*
  * Eigenvalues of the symmetric n x n matrix A (Algorithm 4.3):
- * full-to-band to half-bandwidth b0, halvings b0 -> ... -> 1, bisection.
+ * full-to-band to half-bandwidth b0, band-to-band stages down to the
+ * tridiagonal (b0 -> w -> 1, w the widest of 32 (16 in FP64), 16, 8, 4, 2
+ * that divides b0; straight to 1 from b0 <= 32), bisection.
  *   A      device, n x n, leading dimension lda >= max(1, n); double for
  *          SEV_FP64, float for SEV_MIXED; lower triangle read, overwritten.
  *   b0     first half-bandwidth, 1 <= b0 (values >= n-1 skip full-to-band);
@@ -160,6 +162,52 @@ int sev_tridiag_bisect(sev_handle handle, int n, const double *d, const double *
  * without ordering between them) race and must be serialised by the caller.
  */
 int sev_tridiag_bisect_static(int n, const double *d, const double *e, double rtol, double *eigs, void *stream);
+
+/*
+ * Batched eigenvalues of `count` independent symmetric matrices (no
+ * counterpart in the paper, which treats one matrix; for workloads of many
+ * small uneven matrices such as a sequence of SCF eigenproblems).  Each
+ * matrix follows the same path as sev_eigvalsh: full-to-band with band
+ * width b (Algorithm 4.1; per panel a one-leaf tree QR, Algorithm 3.2, the
+ * compact-WY T and the update of Eq. 4.1), b -> 1 (Algorithm 4.2), Sturm
+ * bisection (rtol 1e-14 FP64, 1e-9 mixed).
+ *
+ * A plan fixes the batch: host arrays n[count], lda[count] (lda[i] >= n[i]),
+ * A[count] (device pointers to the matrices; float for SEV_MIXED, double for
+ * SEV_FP64; lower triangle read, both triangles overwritten) and
+ * eigs[count] (device pointers, n[i] doubles each, ascending on
+ * completion).  The host arrays are read during sev_batch_plan_create only;
+ * the device buffers must stay valid while the plan is run.
+ *   b      band width of the batched kernel: 4, 8, 16 or 32 (32: SEV_MIXED
+ *          only); 0 takes the value sev_batch_autotune chose on this handle
+ *          for prec, else 16 (SEV_MIXED) or 8 (SEV_FP64).
+ * Matrices with n <= 1024 whose path fits one CTA's shared memory run in ONE
+ * persistent launch (each CTA takes matrices largest first from a device
+ * queue); the others run through sev_eigvalsh one after another on the
+ * handle's stream.  Plan creation allocates the descriptor table and
+ * reserves the handle's workspace and synchronises; sev_batch_run only
+ * enqueues work (no allocation, no host synchronisation) and may be
+ * captured in a CUDA graph when every matrix runs in the batched launch
+ * (sev_batch_plan_info reports large_count == 0).  Errors as sev_eigvalsh.
+ */
+typedef struct sev_batch_s *sev_batch_plan;
+int sev_batch_plan_create(sev_handle handle, int count, const int *n, const int *lda, void *const *A,
+                          double *const *eigs, int b, int prec, sev_batch_plan *plan);
+int sev_batch_run(sev_handle handle, sev_batch_plan plan);
+int sev_batch_plan_destroy(sev_batch_plan plan);
+/* Band width, number of matrices in the batched launch, number run one by one. */
+int sev_batch_plan_info(sev_batch_plan plan, int *b, int *small_count, int *large_count);
+/* create + run + synchronise + destroy. */
+int sev_eigvalsh_batched(sev_handle handle, int count, const int *n, const int *lda, void *const *A, int b, int prec,
+                         double *const *eigs);
+/*
+ * Autotuner of the batched band width: times the batched launch on
+ * synthetic matrices with a strided sample (at most 512) of the sizes n[]
+ * for every supported b, stores the fastest in the handle (used when a plan
+ * passes b = 0) and returns it in *b_best (0 if no size fits the batched
+ * kernel).  Allocates and synchronises.
+ */
+int sev_batch_autotune(sev_handle handle, int count, const int *n, int prec, int *b_best);
 
 /* Copy the diagonal and first subdiagonal of a packed band (float or double
  * by prec) into FP64 device arrays d (n) and e (n-1). */

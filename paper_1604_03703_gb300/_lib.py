@@ -47,6 +47,14 @@ SIGNATURES = {
     "sev_kernel_count": (_i, []),
     "sev_kernel_name": (ctypes.c_char_p, [_i]),
     "sev_kernel_time": (_i, [_vp, _i, ctypes.POINTER(_d), ctypes.POINTER(_l), _i]),
+    "sev_batch_plan_create": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_vp),
+                                   ctypes.POINTER(_vp), _i, _i, ctypes.POINTER(_vp)]),
+    "sev_batch_run": (_i, [_vp, _vp]),
+    "sev_batch_plan_destroy": (_i, [_vp]),
+    "sev_batch_plan_info": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "sev_eigvalsh_batched": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_vp), _i, _i,
+                                  ctypes.POINTER(_vp)]),
+    "sev_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
 }
 
 _lib = None

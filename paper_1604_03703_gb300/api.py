@@ -136,6 +136,43 @@ class Handle:
         check(self._lib.sev_tridiag_bisect(self._h, n, _ptr(d), _ptr(ee), float(rtol), _ptr(out)), "sev_tridiag_bisect")
         return out
 
+    # --------------------------------------------------------------- batches
+    def _batch_arrays(self, mats, outs):
+        k = len(mats)
+        n = (ctypes.c_int * max(k, 1))(*[m.shape[0] for m in mats])
+        ld = (ctypes.c_int * max(k, 1))(*[_square_ld(m) for m in mats])
+        A = (ctypes.c_void_p * max(k, 1))(*[m.data_ptr() for m in mats])
+        E = (ctypes.c_void_p * max(k, 1))(*[o.data_ptr() for o in outs])
+        return k, n, ld, A, E
+
+    def _batch_prec(self, mats):
+        precs = {_prec_of(m) for m in mats}
+        if len(precs) > 1:
+            raise ValueError("a batch must be all float32 or all float64")
+        return precs.pop() if precs else _lib.SEV_MIXED
+
+    def eigvalsh_batched(self, mats, b: int = 0, outs=None):
+        """Eigenvalues (ascending, float64) of every symmetric matrix in
+        `mats` (CUDA tensors, all float32 or all float64); overwritten."""
+        self._sync_stream()
+        if outs is None:
+            outs = [torch.empty(m.shape[0], dtype=torch.float64, device=m.device) for m in mats]
+        k, n, ld, A, E = self._batch_arrays(mats, outs)
+        check(self._lib.sev_eigvalsh_batched(self._h, k, n, ld, A, b, self._batch_prec(mats), E),
+              "sev_eigvalsh_batched")
+        return outs
+
+    def batch_plan(self, mats, outs, b: int = 0) -> "BatchPlan":
+        """A plan over fixed matrices and output buffers; run() only enqueues
+        kernels (capturable in a CUDA graph when large_count == 0)."""
+        return BatchPlan(self, mats, outs, b)
+
+    def batch_autotune(self, sizes, prec: int) -> int:
+        arr = (ctypes.c_int * max(len(sizes), 1))(*sizes)
+        best = ctypes.c_int()
+        check(self._lib.sev_batch_autotune(self._h, len(sizes), arr, prec, ctypes.byref(best)), "sev_batch_autotune")
+        return best.value
+
     def get_error(self) -> int:
         return self._lib.sev_get_error(self._h)
 
@@ -179,6 +216,35 @@ class Handle:
             check(self._lib.sev_set_workspace(self._h, ctypes.c_void_p(0), 0), "sev_set_workspace")
         else:
             check(self._lib.sev_set_workspace(self._h, _ptr(buf), buf.numel() * buf.element_size()), "sev_set_workspace")
+
+
+class BatchPlan:
+    def __init__(self, h: Handle, mats, outs, b: int = 0):
+        self.h = h
+        self._keep = (list(mats), list(outs))
+        k, n, ld, A, E = h._batch_arrays(mats, outs)
+        p = ctypes.c_void_p()
+        check(h._lib.sev_batch_plan_create(h._h, k, n, ld, A, E, b, h._batch_prec(mats), ctypes.byref(p)),
+              "sev_batch_plan_create")
+        self._p = p
+        bb, sc, lc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        check(h._lib.sev_batch_plan_info(p, ctypes.byref(bb), ctypes.byref(sc), ctypes.byref(lc)), "sev_batch_plan_info")
+        self.b, self.small_count, self.large_count = bb.value, sc.value, lc.value
+
+    def run(self) -> None:
+        self.h._sync_stream()
+        check(self.h._lib.sev_batch_run(self.h._h, self._p), "sev_batch_run")
+
+    def close(self) -> None:
+        if getattr(self, "_p", None):
+            self.h._lib.sev_batch_plan_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 _default = {}

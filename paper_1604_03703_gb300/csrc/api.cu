@@ -6,6 +6,9 @@
 #include <cstring>
 #include <new>
 
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace sev {
@@ -15,7 +18,7 @@ const char *const kKernelNames[K_COUNT] = {
     "tsqr_leaf_qr", "tsqr_node_qr", "tsqr_node_apply", "tsqr_leaf_apply", "recon_lu",
     "recon_u2",     "symm",         "vform_xt",        "vform_utx",       "vform_reduce",
     "vform_v",      "syr2k",        "split_bf16",      "syr2k_tc",        "symm_tc",
-    "misc"};
+    "batch",        "misc"};
 
 static cudaEvent_t pool_get(sev_ctx *h) {
     if (!h->event_pool.empty()) {
@@ -180,6 +183,50 @@ static int eigvalsh_t(sev_ctx *h, int n, T *A, int lda, int b0, double *eigs) {
     const double rtol = sizeof(T) == 8 ? 1e-14 : 1e-9;
     return launch_bisect(h, n, d, e, rtol, eigs, stage, stage_bytes);
 }
+
+}  // namespace sev
+
+// ------------------------------------------------------------ batched plan
+// A plan fixes the matrices (device pointers, orders, leading dimensions)
+// and the band width of one batch, uploads the per-matrix descriptors once
+// and reserves every workspace, so that running it only launches kernels.
+// Matrices whose whole path fits one CTA's shared memory go to the batched
+// kernel (batched.cu), largest first; the others run the single-matrix path
+// one after another on the handle's stream.
+struct sev_batch_s {
+    int device = 0;
+    int prec = SEV_MIXED;
+    int b = 0;             // band width of the batched kernel
+    int small_count = 0;   // matrices in the batched kernel
+    int nmax_small = 0;
+    int grid = 0;          // persistent CTAs of the batched launch
+    void *d_mats = nullptr;  // descriptors (largest first), then the queue counter
+    int *d_queue = nullptr;
+    struct Big {
+        void *A;
+        double *eigs;
+        int n, lda;
+    };
+    std::vector<Big> big;
+};
+
+namespace sev {
+
+static int g_batch_small_max = 1024;
+
+static int batch_default_b(sev_ctx *h, int prec) {
+    const int tuned = prec == SEV_FP64 ? h->batch_b_fp64 : h->batch_b_mixed;
+    if (tuned > 0) return tuned;
+    return prec == SEV_FP64 ? 8 : 16;
+}
+
+static bool batch_fits(sev_ctx *h, int prec, int b, int n) {
+    if (n > g_batch_small_max) return false;
+    const size_t s = prec == SEV_FP64 ? batch_smem_bytes<double>(b, n) : batch_smem_bytes<float>(b, n);
+    return s > 0 && s <= h->smem_optin;
+}
+
+static double batch_rtol(int prec) { return prec == SEV_FP64 ? 1e-14 : 1e-9; }
 
 }  // namespace sev
 
@@ -387,6 +434,215 @@ int sev_band_tridiag_extract(sev_handle h, int n, const void *AB, int ldab, int 
     if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
     return prec == SEV_FP64 ? launch_tridiag_extract<double>(h, n, (const double *)AB, ldab, d, e ? e : d)
                             : launch_tridiag_extract<float>(h, n, (const float *)AB, ldab, d, e ? e : d);
+}
+
+int sev_batch_plan_create(sev_handle h, int count, const int *n, const int *lda, void *const *A, double *const *eigs,
+                          int b, int prec, sev_batch_plan *plan) {
+    if (!plan) return -9;
+    *plan = nullptr;
+    if (!h) return -1;
+    if (count < 0) return -2;
+    if (count > 0 && (!n || !lda || !A || !eigs)) return -3;
+    if (b < 0) return -7;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -8;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] < 0) return -3;
+        if (n[i] > 0 && (!A[i] || !eigs[i] || lda[i] < n[i])) return -3;
+    }
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    if (b == 0) b = batch_default_b(h, prec);
+    if (!batch_supported(b, prec == SEV_FP64 ? 8 : 4)) return SEV_ERR_UNSUPPORTED;
+    sev_batch_s *P = new (std::nothrow) sev_batch_s();
+    if (!P) return SEV_ERR_WORKSPACE;
+    P->device = h->device;
+    P->prec = prec;
+    P->b = b;
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i) {
+        if (n[i] <= 0) continue;
+        if (batch_fits(h, prec, b, n[i]))
+            order.push_back(i);
+        else
+            P->big.push_back({A[i], eigs[i], n[i], lda[i]});
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return n[x] > n[y]; });
+    P->small_count = (int)order.size();
+    P->nmax_small = order.empty() ? 0 : n[order[0]];
+    if (!order.empty()) {
+        const size_t mb = batch_mat_bytes();
+        const size_t bytes = ((mb * order.size() + 255) & ~(size_t)255) + 256;
+        std::vector<unsigned char> host(bytes, 0);
+        for (size_t k = 0; k < order.size(); ++k) {
+            const int i = order[k];
+            batch_pack_mat(host.data() + k * mb, A[i], eigs[i], n[i], lda[i]);
+        }
+        if (cudaMalloc(&P->d_mats, bytes) != cudaSuccess) {
+            delete P;
+            return SEV_ERR_WORKSPACE;
+        }
+        if (cudaMemcpy(P->d_mats, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(P->d_mats);
+            delete P;
+            return SEV_ERR_CUDA;
+        }
+        P->d_queue = (int *)((char *)P->d_mats + bytes - 256);
+        const int rc = prec == SEV_FP64 ? prepare_batch_small<double>(h, P->small_count, b, P->nmax_small, &P->grid)
+                                        : prepare_batch_small<float>(h, P->small_count, b, P->nmax_small, &P->grid);
+        if (rc) {
+            cudaFree(P->d_mats);
+            delete P;
+            return rc;
+        }
+    }
+    // reserve the single-matrix workspace now, so that running the plan allocates nothing
+    size_t need = 0;
+    for (const auto &g : P->big) {
+        const int b0 = default_b0(g.n, prec);
+        const size_t w = prec == SEV_FP64 ? eig_workspace<double>(h, g.n, b0 > g.n - 1 ? g.n - 1 : b0)
+                                          : eig_workspace<float>(h, g.n, b0 > g.n - 1 ? g.n - 1 : b0);
+        if (w > need) need = w;
+    }
+    if (need) {
+        void *ws = nullptr;
+        const int rc = get_workspace(h, need, &ws);
+        if (rc) {
+            if (P->d_mats) cudaFree(P->d_mats);
+            delete P;
+            return rc;
+        }
+    }
+    *plan = P;
+    return SEV_OK;
+}
+
+int sev_batch_run(sev_handle h, sev_batch_plan P) {
+    if (!h) return -1;
+    if (!P) return -2;
+    if (P->device != h->device) return -2;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    int rc = SEV_OK;
+    if (P->small_count > 0) {
+        rc = P->prec == SEV_FP64
+                 ? launch_batch_small<double>(h, P->small_count, P->d_mats, P->d_queue, P->b, P->nmax_small,
+                                              batch_rtol(P->prec), P->grid)
+                 : launch_batch_small<float>(h, P->small_count, P->d_mats, P->d_queue, P->b, P->nmax_small,
+                                             batch_rtol(P->prec), P->grid);
+        if (rc) return rc;
+    }
+    for (const auto &g : P->big) {
+        rc = sev_eigvalsh(h, g.n, g.A, g.lda, 0, P->prec, g.eigs);
+        if (rc) return rc;
+    }
+    return SEV_OK;
+}
+
+int sev_batch_plan_destroy(sev_batch_plan P) {
+    if (!P) return -1;
+    if (P->d_mats) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        cudaSetDevice(P->device);
+        cudaFree(P->d_mats);
+        cudaSetDevice(cur);
+    }
+    delete P;
+    return SEV_OK;
+}
+
+int sev_batch_plan_info(sev_batch_plan P, int *b, int *small_count, int *large_count) {
+    if (!P) return -1;
+    if (b) *b = P->b;
+    if (small_count) *small_count = P->small_count;
+    if (large_count) *large_count = (int)P->big.size();
+    return SEV_OK;
+}
+
+int sev_eigvalsh_batched(sev_handle h, int count, const int *n, const int *lda, void *const *A, int b, int prec,
+                         double *const *eigs) {
+    sev_batch_plan P = nullptr;
+    int rc = sev_batch_plan_create(h, count, n, lda, A, eigs, b, prec, &P);
+    if (rc) return rc;
+    rc = sev_batch_run(h, P);
+    // the descriptors must outlive the launch
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess && rc == SEV_OK) rc = SEV_ERR_CUDA;
+    sev_batch_plan_destroy(P);
+    return rc;
+}
+
+int sev_batch_autotune(sev_handle h, int count, const int *n, int prec, int *b_best) {
+    if (!h) return -1;
+    if (count < 0) return -2;
+    if (count > 0 && !n) return -3;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -4;
+    if (!b_best) return -5;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    const int elem = prec == SEV_FP64 ? 8 : 4;
+    const int cands[] = {4, 8, 16, 32};
+    // a strided sample (at most 512) of the sizes that fit the batched kernel at the narrowest band
+    std::vector<int> sizes;
+    for (int i = 0; i < count; ++i)
+        if (n[i] > 0 && batch_fits(h, prec, 8, n[i])) sizes.push_back(n[i]);
+    std::sort(sizes.begin(), sizes.end());
+    std::vector<int> sample;
+    const size_t want = sizes.size() < 512 ? sizes.size() : 512;
+    for (size_t k = 0; k < want; ++k) sample.push_back(sizes[k * sizes.size() / want]);
+    *b_best = 0;
+    if (sample.empty()) return SEV_OK;
+    size_t total = 0;
+    std::vector<size_t> off;
+    for (int m : sample) {
+        off.push_back(total);
+        total += (((size_t)elem * m * m + 255) & ~(size_t)255) + (((size_t)8 * m + 255) & ~(size_t)255);
+    }
+    void *buf = nullptr;
+    if (cudaMalloc(&buf, total) != cudaSuccess) return SEV_ERR_WORKSPACE;
+    std::vector<void *> As(sample.size());
+    std::vector<double *> Es(sample.size());
+    for (size_t k = 0; k < sample.size(); ++k) {
+        As[k] = (char *)buf + off[k];
+        Es[k] = (double *)((char *)As[k] + (((size_t)elem * sample[k] * sample[k] + 255) & ~(size_t)255));
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 0.f;
+    int rc = SEV_OK;
+    for (int b : cands) {
+        if (!batch_supported(b, elem)) continue;
+        bool ok = true;
+        for (int m : sample) ok = ok && batch_fits(h, prec, b, m);
+        if (!ok) continue;
+        sev_batch_plan P = nullptr;
+        rc = sev_batch_plan_create(h, (int)sample.size(), sample.data(), sample.data(), As.data(), Es.data(), b, prec,
+                                   &P);
+        if (rc) break;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && rc == SEV_OK; ++rep) {  // warm-up, then timed
+            rc = prec == SEV_FP64 ? launch_batch_fill<double>(h, P->small_count, P->d_mats, 0x5EEDull)
+                                  : launch_batch_fill<float>(h, P->small_count, P->d_mats, 0x5EEDull);
+            if (rc) break;
+            cudaEventRecord(e0, h->stream);
+            rc = sev_batch_run(h, P);
+            cudaEventRecord(e1, h->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) rc = SEV_ERR_CUDA;
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        sev_batch_plan_destroy(P);
+        if (rc) break;
+        if (*b_best == 0 || ms < best_ms) {
+            best_ms = ms;
+            *b_best = b;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    if (rc) return rc;
+    if (prec == SEV_FP64)
+        h->batch_b_fp64 = *b_best;
+    else
+        h->batch_b_mixed = *b_best;
+    return SEV_OK;
 }
 
 int sev_get_error(sev_handle h) {

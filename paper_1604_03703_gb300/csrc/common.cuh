@@ -38,6 +38,7 @@ enum KernelId {
     K_SPLIT_BF16,
     K_SYR2K_TC,
     K_SYMM_TC,
+    K_BATCH,
     K_MISC,
     K_COUNT
 };
@@ -65,6 +66,8 @@ struct sev_ctx {
     size_t h_stage_bytes = 0;
     unsigned long long timing = 0;  // bit k: time kernel id k
     int leaf_rows_override = 0;  // SEV_LEAF_ROWS: rows per tree-QR leaf (tests)
+    int batch_b_fp64 = 0;        // band width chosen by sev_batch_autotune (0: default)
+    int batch_b_mixed = 0;
     std::vector<sev::TimedLaunch> pending;
     std::vector<cudaEvent_t> event_pool;
     double tot_ms[sev::K_COUNT] = {};
@@ -526,6 +529,19 @@ int band_tri_supported(int b, int elem);
 size_t band_tri_workspace(int n);
 template <typename T>
 int launch_band_tri(sev_ctx *h, int n, T *AB, int ldab, int b, void *ws, size_t ws_bytes);
+
+// batched.cu: one CTA per matrix, whole path, persistent over a queue
+int batch_supported(int b, int elem);
+template <typename T>
+size_t batch_smem_bytes(int b, int nmax);
+template <typename T>
+int prepare_batch_small(sev_ctx *h, int count, int b, int nmax, int *grid);
+template <typename T>
+int launch_batch_small(sev_ctx *h, int count, const void *mats, int *queue, int b, int nmax, double rtol, int grid);
+size_t batch_mat_bytes();
+void batch_pack_mat(void *dst, void *A, double *eigs, int n, int lda);
+template <typename T>
+int launch_batch_fill(sev_ctx *h, int count, const void *mats, unsigned long long seed);
 
 // panel.cu + update.cu
 template <typename T>

@@ -180,3 +180,26 @@ def qdq_torch(D, seed: int, device, dtype=None):
 def batch_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Matrix orders drawn uniformly from lo..hi inclusive."""
     return rng(seed).integers(lo, hi + 1, size=count)
+
+
+def batch_small(count: int = 4096, seed: int = SEED_BASE + 3):
+    """The many-small-matrices workload: orders uniform in 32..512, each a
+    symmetric N(0,1)/sqrt(n) matrix (seed + 1 + index)."""
+    sizes = batch_sizes(count, 32, 512, seed)
+    return [semicircle(int(m), seed + 1 + k) for k, m in enumerate(sizes)]
+
+
+def batch_scf(count: int = 64, seed: int = SEED_BASE + 4):
+    """The SCF-like sequence: orders uniform in 1024..6144; per distinct
+    order one A0 = Q diag(D) Q^T with D uniform in [-10, 10]; matrix k is
+    A0(n_k) + 1e-3 E_k with E_k a symmetric N(0,1)/sqrt(n) matrix."""
+    sizes = batch_sizes(count, 1024, 6144, seed)
+    base = {}
+    out = []
+    for k, m in enumerate(sizes):
+        m = int(m)
+        if m not in base:
+            D = rng(seed + 100000 + m).uniform(-10.0, 10.0, m)
+            base[m] = qdq(D, seed + 200000 + m)
+        out.append(base[m] + 1e-3 * semicircle(m, seed + 1 + k))
+    return out
