@@ -134,9 +134,11 @@ int sev_band_to_band(sev_handle handle, int n, void *AB, int ldab, int b, int h,
 /*
  * All eigenvalues of the symmetric tridiagonal T with diagonal d[0..n-1] and
  * off-diagonal e[0..n-2] (device, double), ascending, into eigs (device,
- * n doubles), by bisection on the Sturm count (negative pivots of
- * LDL^T(T - xI) with the pivmin guard) from the Gershgorin interval, until
- * hi - lo <= max(rtol*max(|lo|,|hi|), rtol*||T||_G) (rtol > 0).
+ * n doubles), by bisection on the Sturm count (sign changes of the leading
+ * principal minors of T - xI, evaluated on T scaled by the power of two
+ * that brings its Gershgorin bound into [0.5, 1)) from the widened
+ * Gershgorin interval, until hi - lo <= max(rtol*max(|lo|,|hi|),
+ * rtol*||T||_G) (rtol > 0).  T = 0 gives exact zeros.
  */
 int sev_tridiag_bisect(sev_handle handle, int n, const double *d, const double *e, double rtol,
                        double *eigs);

@@ -57,6 +57,8 @@ def _load():
             lib.orc_pivmin.argtypes = [i, _dp]
             lib.orc_sturm_count.restype = i
             lib.orc_sturm_count.argtypes = [i, _dp, _dp, d, d]
+            lib.orc_sturm_count_minors.restype = i
+            lib.orc_sturm_count_minors.argtypes = [i, _dp, _dp, d]
             lib.orc_gershgorin.restype = d
             lib.orc_gershgorin.argtypes = [i, _dp, _dp, d, _dp, _dp]
             lib.orc_bisect.restype = i
@@ -136,6 +138,15 @@ def sturm_count(d, e, x: float) -> int:
     e2[: n - 1] = e * e
     pm = pivmin(e)
     return _load().orc_sturm_count(n, _ptr(d), _ptr(e2), float(x), pm)
+
+
+def sturm_count_minors(d, e, x: float) -> int:
+    """Number of eigenvalues of T(d, e) below x: sign changes of the leading
+    principal minors of T - xI on the exactly rescaled matrix (the count
+    the bisection uses)."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    e = np.ascontiguousarray(np.append(np.asarray(e, dtype=np.float64), 0.0))
+    return _load().orc_sturm_count_minors(d.size, _ptr(d), _ptr(e), float(x))
 
 
 def gershgorin(d, e):

@@ -18,9 +18,12 @@
  *                        (Sec. 3.2, Lemma 3.4: Householder form Q = I - U T U^T)
  *   orc_tridiagonalize   unblocked Householder tridiagonalisation: Algorithm
  *                        4.1 with b = 1, the direct reduction of Sec. 4
- *   orc_sturm_count      Sturm count of a symmetric tridiagonal (the final
- *                        eigenvalue step of Algorithm 4.3; bisection method)
- *   orc_bisect           bisection on the Sturm count, eigenvalues ascending
+ *   orc_sturm_count      Sturm count of a symmetric tridiagonal by LDL^T
+ *                        pivots (cross-check of the minors count)
+ *   orc_sturm_minors     Sturm count by the leading principal minors on the
+ *                        exactly rescaled matrix (the count the bisection uses)
+ *   orc_bisect           bisection on the minors count, eigenvalues ascending
+ *                        (the final eigenvalue step of Algorithm 4.3)
  *   orc_eigvalsh         orc_tridiagonalize + orc_bisect (Algorithm 4.3's result)
  *   orc_jacobi           cyclic Jacobi (independent cross-check, n <= ~32)
  *   orc_inertia          LDL^T inertia of A - xI in long double (Sylvester)
@@ -31,6 +34,7 @@
  *                        (A5-A8) of the index sets stated at the function
  */
 #include <float.h>
+#include <stdint.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -194,12 +198,110 @@ double orc_gershgorin(int n, const double *d, const double *e, double pivmin,
 }
 
 /*
+ * Exact power-of-two scaling of T(d, e) for the bisection: s is chosen so
+ * that the Gershgorin bound tnorm = max(|gl|, |gu|) of T scaled by 2^-s lies
+ * in [0.5, 1) (s = 0 for the zero matrix).  Returns s; sc = 2^-s.  Scaling by
+ * a power of two is exact (barring underflow) and scales every eigenvalue by
+ * the same factor, so the bisection runs on the scaled matrix and its
+ * results are scaled back exactly.
+ */
+static int bis_scale(int n, const double *d, const double *e, double *gl_out, double *gu_out, double *tnorm_out)
+{
+    double gl = d[0], gu = d[0];
+    for (int i = 0; i < n; ++i) {
+        double r = 0.0;
+        if (i > 0) r += fabs(e[i - 1]);
+        if (i + 1 < n) r += fabs(e[i]);
+        if (d[i] - r < gl) gl = d[i] - r;
+        if (d[i] + r > gu) gu = d[i] + r;
+    }
+    double tnorm = fabs(gl) > fabs(gu) ? fabs(gl) : fabs(gu);
+    int s = 0;
+    if (tnorm > 0.0) (void)frexp(tnorm, &s); /* tnorm = m 2^s, m in [0.5, 1) */
+    *gl_out = gl;
+    *gu_out = gu;
+    *tnorm_out = tnorm;
+    return s;
+}
+
+static double pow2(int k) /* exact 2^k for -1022 <= k <= 1023 */
+{
+    uint64_t bits = (uint64_t)(1023 + k) << 52;
+    double f;
+    memcpy(&f, &bits, sizeof f);
+    return f;
+}
+
+/*
+ * Sturm count by the leading principal minors of T - xI (Sturm's theorem:
+ * the number of eigenvalues below x is the number of sign changes in
+ * p_0 = 1, p_1, ..., p_n):  p_1 = d_0 - x,
+ *   p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1},
+ * the division-free form of the LDL^T pivot count (q_i = p_i / p_{i-1}).
+ * Works on the scaled matrix: d_i - x is formed as fma(d_i, sc, -x) (one
+ * rounding of the exactly scaled entry minus x) and e2s holds the squared
+ * scaled off-diagonal; each step is u = e2s_{i-1} p_{i-1} followed by
+ * p_{i+1} = fma(d_i - x, p_i, -u).  A minor equal to zero takes the sign
+ * opposite to its predecessor (it counts as a change, as a zero pivot does
+ * under the pivmin rule).  Whenever |p_i| leaves [2^-256, 2^256] the pair
+ * (p_{i-1}, p_i) is rescaled by the power of two 2^k, k = clamp(-exponent,
+ * -512, 512), bringing p_i to [1, 2): signs are unchanged and nothing
+ * overflows for a scaled matrix (|d_i - x| <= 2, e2s <= 1).
+ */
+int orc_sturm_minors(int n, const double *d, const double *e2s, double sc, double x)
+{
+    double a = 1.0, b = fma(d[0], sc, -x);
+    int neg = b <= 0.0; /* p_0 = 1 > 0: a zero p_1 counts as negative */
+    int c = neg;
+    for (int i = 1; i < n; ++i) {
+        double t = fma(d[i], sc, -x);
+        double u = e2s[i - 1] * a;
+        double p = fma(t, b, -u);
+        int pn = (p < 0.0) || (p == 0.0 && !neg);
+        c += pn != neg;
+        neg = pn;
+        a = b;
+        b = p;
+        uint64_t bits;
+        memcpy(&bits, &b, sizeof bits);
+        int ex = (int)((bits >> 52) & 0x7FF);
+        if (ex > 1023 + 256 || (ex < 1023 - 256 && b != 0.0)) {
+            int k = 1023 - ex;
+            if (k > 512) k = 512;
+            if (k < -512) k = -512;
+            double f = pow2(k);
+            a *= f;
+            b *= f;
+        }
+    }
+    return c;
+}
+
+/* The minors count of T(d, e) at x for unscaled inputs (scales first). */
+int orc_sturm_count_minors(int n, const double *d, const double *e, double x)
+{
+    double gl, gu, tn;
+    int s = bis_scale(n, d, e, &gl, &gu, &tn);
+    double sc = pow2(-s);
+    double *e2s = (double *)malloc(sizeof(double) * (size_t)(n > 1 ? n : 1));
+    for (int i = 0; i + 1 < n; ++i) {
+        double es = e[i] * sc;
+        e2s[i] = es * es;
+    }
+    int c = orc_sturm_minors(n, d, e2s, sc, x * sc);
+    free(e2s);
+    return c;
+}
+
+/*
  * Bisection for every eigenvalue of T(d, e), ascending (index k = 0..n-1 is
- * the (k+1)-th smallest).  For each k: [lo, hi] = widened Gershgorin
- * interval; mid = 0.5*(lo + hi); count(mid) >= k+1 -> hi = mid, else
- * lo = mid; stop when hi - lo <= max(rtol*max(|lo|,|hi|), rtol*tnorm), when
- * mid no longer splits the interval, or after maxit steps; eig = 0.5*(lo+hi).
- * Returns the number of eigenvalues that hit maxit before converging.
+ * the (k+1)-th smallest), on the matrix scaled by 2^-s (bis_scale):
+ * [lo, hi] = the scaled Gershgorin interval widened by 2 n eps tnorm + 2^-1000;
+ * mid = 0.5*(lo + hi); minors count(mid) >= k+1 -> hi = mid, else lo = mid;
+ * stop when hi - lo <= max(rtol*max(|lo|,|hi|), rtol*tnorm), when mid no
+ * longer splits the interval, or after maxit steps; eig = 2^s * 0.5*(lo+hi).
+ * T = 0 (a zero Gershgorin bound) gives exact zeros.  Returns the number
+ * of eigenvalues that hit maxit before converging.
  */
 int orc_bisect_range(int n, const double *d, const double *e, double rtol, int maxit, int k0, int k1,
                      double *eigs);
@@ -219,12 +321,25 @@ int orc_bisect_range(int n, const double *d, const double *e, double rtol, int m
         if (k0 == 0 && k1 > 0) eigs[0] = d[0];
         return 0;
     }
-    double *e2 = (double *)malloc(sizeof(double) * (size_t)n);
-    for (int i = 0; i + 1 < n; ++i) e2[i] = e[i] * e[i];
-    e2[n - 1] = 0.0;
-    double pivmin = orc_pivmin(n, e);
-    double gl, gu;
-    double tnorm = orc_gershgorin(n, d, e, pivmin, &gl, &gu);
+    double gl, gu, tnorm;
+    int s = bis_scale(n, d, e, &gl, &gu, &tnorm);
+    if (tnorm == 0.0) { /* a zero Gershgorin bound means T = 0 */
+        for (int k = k0; k < k1; ++k) eigs[k - k0] = 0.0;
+        return 0;
+    }
+    double sc = pow2(-s), up = pow2(s);
+    double *e2s = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i + 1 < n; ++i) {
+        double es = e[i] * sc;
+        e2s[i] = es * es;
+    }
+    e2s[n - 1] = 0.0;
+    gl *= sc;
+    gu *= sc;
+    tnorm *= sc;
+    double pad = 2.0 * (double)n * DBL_EPSILON * tnorm + 0x1p-1000;
+    gl -= pad;
+    gu += pad;
     double atol = rtol * tnorm;
     int noconv = 0;
     for (int k = k0; k < k1; ++k) {
@@ -242,15 +357,15 @@ int orc_bisect_range(int n, const double *d, const double *e, double rtol, int m
             }
             double mid = 0.5 * (lo + hi);
             if (mid <= lo || mid >= hi) break;
-            if (orc_sturm_count(n, d, e2, mid, pivmin) >= k + 1)
+            if (orc_sturm_minors(n, d, e2s, sc, mid) >= k + 1)
                 hi = mid;
             else
                 lo = mid;
             ++it;
         }
-        eigs[k - k0] = 0.5 * (lo + hi);
+        eigs[k - k0] = (0.5 * (lo + hi)) * up;
     }
-    free(e2);
+    free(e2s);
     return noconv;
 }
 

@@ -194,17 +194,35 @@ __device__ bool batch_band_to_tri(const T *A, int n, int lda, unsigned char *sme
 }
 
 // -------------------------------------------------------------- bisection
-// The same recurrence, stopping rule and IEEE operations as bisect.cu, on
-// shared-memory d and e^2.
-__device__ __forceinline__ int batch_sturm(int n, const double *d, const double *e2, double x, double pivmin) {
-    int c = 0;
-    double q = __dsub_rn(d[0], x);
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+// The same scaling, minors count, stopping rule and IEEE operations as
+// bisect.cu, on shared-memory d and (e 2^-s)^2.
+__device__ __forceinline__ double batch_pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+__device__ __forceinline__ int batch_sturm(int n, const double *d, const double *e2s, double x, double sc) {
+    double a = 1.0, b = __fma_rn(d[0], sc, -x);
+    bool neg = b <= 0.0;
+    int c = neg;
     for (int i = 1; i < n; ++i) {
-        q = __dsub_rn(__dsub_rn(d[i], x), __ddiv_rn(e2[i - 1], q));
-        if (fabs(q) < pivmin) q = -pivmin;
-        c += q < 0.0;
+        const double t = __fma_rn(d[i], sc, -x);
+        const double u = __dmul_rn(e2s[i - 1], a);
+        const double p = __fma_rn(t, b, -u);
+        // sign, zero test and exponent from the bits: integer work, so the
+        // FP64 pipe sees only the three operations above
+        const long long pb = __double_as_longlong(p);
+        const bool zero = (pb << 1) == 0;
+        const bool pn = zero ? !neg : pb < 0;
+        c += pn != neg;
+        neg = pn;
+        a = b;
+        b = p;
+        const int ex = (int)((pb >> 52) & 0x7FF);
+        if (__builtin_expect(ex > 1023 + 256 || (ex < 1023 - 256 && !zero), 0)) {
+            int k = 1023 - ex;
+            k = k > 512 ? 512 : (k < -512 ? -512 : k);
+            const double f = batch_pow2(k);
+            a = __dmul_rn(a, f);
+            b = __dmul_rn(b, f);
+        }
     }
     return c;
 }
@@ -216,50 +234,58 @@ __device__ void batch_bisect(int n, int nmax, unsigned char *smem, double rtol, 
     const T *band = (const T *)smem;
     double *d = (double *)(smem + BatchLayout<T, B>::e_off(nmax));
     double *e = d + nmax;
-    double *e2 = e + nmax;
-    double *par = e2 + nmax;  // gl, gu, pivmin, tnorm
-    double *red = par + 8;    // 32
+    double *e2s = e + nmax;
+    double *par = e2s + nmax;  // gl, gu, sc, tnorm, 2^s, zero
+    double *red = par + 8;     // 32
     for (int i = tid; i < n; i += nt) {
         d[i] = (double)band[(size_t)i * LDW];
         e[i] = i + 1 < n ? (double)band[(size_t)i * LDW + 1] : 0.0;
     }
     __syncthreads();
-    double lo = INFINITY, hi = -INFINITY, emax = 1.0;
+    double lo = INFINITY, hi = -INFINITY;
     for (int i = tid; i < n; i += nt) {
         double r = 0.0;
         if (i > 0) r = __dadd_rn(r, fabs(e[i - 1]));
-        if (i + 1 < n) {
-            r = __dadd_rn(r, fabs(e[i]));
-            const double t = __dmul_rn(e[i], e[i]);
-            e2[i] = t;
-            emax = fmax(emax, t);
-        } else {
-            e2[i] = 0.0;
-        }
+        if (i + 1 < n) r = __dadd_rn(r, fabs(e[i]));
         lo = fmin(lo, __dsub_rn(d[i], r));
         hi = fmax(hi, __dadd_rn(d[i], r));
     }
     lo = -block_max(-lo, red);
     hi = block_max(hi, red);
-    emax = block_max(emax, red);
     if (tid == 0) {
-        const double pivmin = __dmul_rn(DBL_MIN, emax);
-        const double tnorm = fmax(fabs(lo), fabs(hi));
-        const double pad = __dadd_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, (double)n), DBL_EPSILON), tnorm),
-                                     __dmul_rn(4.0, pivmin));
+        double tnorm = fmax(fabs(lo), fabs(hi));
+        if (!isfinite(tnorm)) latch_error(err, SEV_ERR_NONFINITE);
+        int s = 0;
+        if (tnorm > 0.0 && isfinite(tnorm)) (void)frexp(tnorm, &s);
+        const double sc = batch_pow2(-s);
+        lo = __dmul_rn(lo, sc);
+        hi = __dmul_rn(hi, sc);
+        tnorm = __dmul_rn(tnorm, sc);
+        const double pad = __dadd_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, (double)n), DBL_EPSILON), tnorm), 0x1p-1000);
         par[0] = __dsub_rn(lo, pad);
         par[1] = __dadd_rn(hi, pad);
-        par[2] = pivmin;
+        par[2] = sc;
         par[3] = tnorm;
-        if (!isfinite(tnorm)) latch_error(err, SEV_ERR_NONFINITE);
+        par[4] = batch_pow2(s);
+        par[5] = tnorm == 0.0 ? 1.0 : 0.0;
     }
     __syncthreads();
-    const double pivmin = par[2];
+    const double sc = par[2];
+    for (int i = tid; i < n; i += nt) {
+        if (i + 1 < n) {
+            const double es = __dmul_rn(e[i], sc);
+            e2s[i] = __dmul_rn(es, es);
+        } else {
+            e2s[i] = 0.0;
+        }
+    }
+    __syncthreads();
     const double atol = __dmul_rn(rtol, par[3]);
+    const bool zero = par[5] != 0.0;
     for (int k = tid; k < n; k += nt) {
         double a = par[0], b = par[1];
         int it = 0;
-        for (;;) {
+        for (; !zero;) {
             const double w = __dsub_rn(b, a);
             const double mag = fmax(fabs(a), fabs(b));
             double tol = __dmul_rn(rtol, mag);
@@ -271,13 +297,13 @@ __device__ void batch_bisect(int n, int nmax, unsigned char *smem, double rtol, 
             }
             const double mid = __dmul_rn(0.5, __dadd_rn(a, b));
             if (mid <= a || mid >= b) break;
-            if (batch_sturm(n, d, e2, mid, pivmin) >= k + 1)
+            if (batch_sturm(n, d, e2s, mid, sc) >= k + 1)
                 b = mid;
             else
                 a = mid;
             ++it;
         }
-        eigs[k] = __dmul_rn(0.5, __dadd_rn(a, b));
+        eigs[k] = zero ? 0.0 : __dmul_rn(__dmul_rn(0.5, __dadd_rn(a, b)), par[4]);
     }
     __syncthreads();
 }

@@ -2,12 +2,17 @@
 // bisection (the "compute its eigenvalues" step of Algorithm 4.3), plus the
 // small copy kernels between dense, packed-band and tridiagonal storage.
 //
-// The Sturm count at x is the number of negative pivots of LDL^T(T - xI):
-//   q_0 = d_0 - x,  q_i = (d_i - x) - e_{i-1}^2 / q_{i-1},
-// with |q_i| < pivmin replaced by -pivmin, pivmin = DBL_MIN max(1, max e^2).
-// Every FP64 operation is written with an explicit round-to-nearest
-// intrinsic so no multiply-add is contracted: the result is the exact IEEE
-// evaluation of the recurrence in the order written.
+// The bisection runs on T scaled by an exact power of two 2^-s that brings
+// its Gershgorin bound into [0.5, 1).  The Sturm count at x is the number of
+// sign changes of the leading principal minors of T - xI (Sturm's theorem),
+//   p_1 = d_0 - x,  p_{i+1} = (d_i - x) p_i - e_{i-1}^2 p_{i-1},
+// the division-free form of the LDL^T pivot count: per step one FMA on the
+// dependence chain (instead of a ~1000-cycle FP64 division), the pair
+// (p_{i-1}, p_i) rescaled by a power of two when |p_i| leaves
+// [2^-256, 2^256], a zero minor counted as a sign change.  Every FP64
+// operation is written with an explicit round-to-nearest intrinsic so no
+// multiply-add is contracted: the result is the exact IEEE evaluation of the
+// recurrence in the order written.
 #include "common.cuh"
 
 namespace sev {
@@ -59,56 +64,89 @@ template int launch_tridiag_extract<float>(sev_ctx *, int, const float *, int, d
 template int launch_tridiag_extract<double>(sev_ctx *, int, const double *, int, double *, double *);
 
 // ----------------------------------------------------------------- bisection
-// par[0] = gl, par[1] = gu (widened Gershgorin interval), par[2] = pivmin,
-// par[3] = tnorm (max |end| of the unwidened interval).
+// par[0] = gl, par[1] = gu (scaled, widened Gershgorin interval), par[2] = sc
+// = 2^-s, par[3] = tnorm (scaled max |end| of the unwidened interval),
+// par[4] = 2^s, par[5] = 1 if T = 0 (a zero Gershgorin bound).  e2s[i] =
+// (e_i 2^-s)^2.
+__device__ __forceinline__ double pow2_exact(int k) {  // 2^k, -1022 <= k <= 1023
+    return __longlong_as_double((long long)(1023 + k) << 52);
+}
+
 __global__ void bisect_prep_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
-                                   double *__restrict__ e2, double *__restrict__ par) {
+                                   double *__restrict__ e2s, double *__restrict__ par) {
     __shared__ double red[32];
-    double lo = INFINITY, hi = -INFINITY, emax = 1.0;
+    __shared__ double s_sc;
+    double lo = INFINITY, hi = -INFINITY;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double r = 0.0;
         if (i > 0) r = __dadd_rn(r, fabs(e[i - 1]));
-        if (i + 1 < n) {
-            r = __dadd_rn(r, fabs(e[i]));
-            const double t = __dmul_rn(e[i], e[i]);
-            e2[i] = t;
-            emax = fmax(emax, t);
-        }
+        if (i + 1 < n) r = __dadd_rn(r, fabs(e[i]));
         lo = fmin(lo, __dsub_rn(d[i], r));
         hi = fmax(hi, __dadd_rn(d[i], r));
     }
     lo = -block_max(-lo, red);
     hi = block_max(hi, red);
-    emax = block_max(emax, red);
     if (threadIdx.x == 0) {
-        const double pivmin = __dmul_rn(DBL_MIN, emax);
-        const double tnorm = fmax(fabs(lo), fabs(hi));
-        const double pad = __dadd_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, (double)n), DBL_EPSILON), tnorm),
-                                     __dmul_rn(4.0, pivmin));
+        double tnorm = fmax(fabs(lo), fabs(hi));
+        int s = 0;
+        if (tnorm > 0.0) (void)frexp(tnorm, &s);  // tnorm = m 2^s, m in [0.5, 1)
+        const double sc = pow2_exact(-s);
+        lo = __dmul_rn(lo, sc);
+        hi = __dmul_rn(hi, sc);
+        tnorm = __dmul_rn(tnorm, sc);
+        const double pad = __dadd_rn(__dmul_rn(__dmul_rn(__dmul_rn(2.0, (double)n), DBL_EPSILON), tnorm), 0x1p-1000);
         par[0] = __dsub_rn(lo, pad);
         par[1] = __dadd_rn(hi, pad);
-        par[2] = pivmin;
+        par[2] = sc;
         par[3] = tnorm;
-        if (n > 0) e2[n - 1] = 0.0;
+        par[4] = pow2_exact(s);
+        par[5] = tnorm == 0.0 ? 1.0 : 0.0;
+        s_sc = sc;
+    }
+    __syncthreads();
+    const double sc = s_sc;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (i + 1 < n) {
+            const double es = __dmul_rn(e[i], sc);
+            e2s[i] = __dmul_rn(es, es);
+        } else {
+            e2s[i] = 0.0;
+        }
     }
 }
 
-__device__ __forceinline__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e2,
-                                           double x, double pivmin) {
-    int c = 0;
-    double q = __dsub_rn(__ldg(d), x);
-    if (fabs(q) < pivmin) q = -pivmin;
-    c += q < 0.0;
+__device__ __forceinline__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e2s,
+                                           double x, double sc) {
+    double a = 1.0, b = __fma_rn(__ldg(d), sc, -x);
+    bool neg = b <= 0.0;  // p_0 = 1 > 0: a zero p_1 counts as negative
+    int c = neg;
     for (int i = 1; i < n; ++i) {
-        q = __dsub_rn(__dsub_rn(__ldg(d + i), x), __ddiv_rn(__ldg(e2 + i - 1), q));
-        if (fabs(q) < pivmin) q = -pivmin;
-        c += q < 0.0;
+        const double t = __fma_rn(__ldg(d + i), sc, -x);
+        const double u = __dmul_rn(__ldg(e2s + i - 1), a);
+        const double p = __fma_rn(t, b, -u);
+        // sign, zero test and exponent from the bits: integer work, so the
+        // FP64 pipe sees only the three operations above
+        const long long pb = __double_as_longlong(p);
+        const bool zero = (pb << 1) == 0;
+        const bool pn = zero ? !neg : pb < 0;
+        c += pn != neg;
+        neg = pn;
+        a = b;
+        b = p;
+        const int ex = (int)((pb >> 52) & 0x7FF);
+        if (__builtin_expect(ex > 1023 + 256 || (ex < 1023 - 256 && !zero), 0)) {
+            int k = 1023 - ex;
+            k = k > 512 ? 512 : (k < -512 ? -512 : k);
+            const double f = pow2_exact(k);
+            a = __dmul_rn(a, f);
+            b = __dmul_rn(b, f);
+        }
     }
     return c;
 }
 
 // One thread per eigenvalue index k (the (k+1)-th smallest).
-__global__ void bisect_kernel(int n, const double *__restrict__ d, const double *__restrict__ e2,
+__global__ void bisect_kernel(int n, const double *__restrict__ d, const double *__restrict__ e2s,
                               const double *__restrict__ par, double rtol, int maxit, double *__restrict__ eigs,
                               int *err) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -117,7 +155,11 @@ __global__ void bisect_kernel(int n, const double *__restrict__ d, const double 
         eigs[0] = d[0];
         return;
     }
-    const double pivmin = par[2];
+    if (par[5] != 0.0) {
+        eigs[k] = 0.0;
+        return;
+    }
+    const double sc = par[2];
     const double atol = __dmul_rn(rtol, par[3]);
     double lo = par[0], hi = par[1];
     int it = 0;
@@ -133,13 +175,13 @@ __global__ void bisect_kernel(int n, const double *__restrict__ d, const double 
         }
         const double mid = __dmul_rn(0.5, __dadd_rn(lo, hi));
         if (mid <= lo || mid >= hi) break;
-        if (sturm_count(n, d, e2, mid, pivmin) >= k + 1)
+        if (sturm_count(n, d, e2s, mid, sc) >= k + 1)
             hi = mid;
         else
             lo = mid;
         ++it;
     }
-    eigs[k] = __dmul_rn(0.5, __dadd_rn(lo, hi));
+    eigs[k] = __dmul_rn(__dmul_rn(0.5, __dadd_rn(lo, hi)), par[4]);
 }
 
 // ------------------------------------------------- shared-interval rounds
@@ -222,12 +264,9 @@ __device__ __forceinline__ int bis_step_test(double lo, double hi, int it, doubl
     return 0;
 }
 
-// The count as a separate (not inlined) function: its loop is compiled on
-// its own, as tight as in bisect_kernel, whatever the round logic around it
-// keeps live.
-__device__ __noinline__ int sturm_chain(int n, const double *__restrict__ d, const double *__restrict__ e2, double x,
-                                        double pivmin) {
-    return sturm_count(n, d, e2, x, pivmin);
+__device__ __forceinline__ int sturm_chain(int n, const double *__restrict__ d, const double *__restrict__ e2s, double x,
+                                        double sc) {
+    return sturm_count(n, d, e2s, x, sc);
 }
 
 struct BisWs {
@@ -247,15 +286,16 @@ __global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const
                                                                     int maxit, int budget, double *__restrict__ eigs,
                                                                     BisWs W, int *err) {
     __shared__ int s_scan[kBisThreads];
-    const double pivmin = par[2];
+    const double sc = par[2];
     const double atol = __dmul_rn(rtol, par[3]);
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gthreads = gridDim.x * blockDim.x;
+    const int zero = par[5] != 0.0;  // T = 0: every eigenvalue is exactly 0 (lo = hi = 0, finished)
     for (int k = gtid; k < n; k += gthreads) {
-        W.lo[k] = par[0];
-        W.hi[k] = par[1];
+        W.lo[k] = zero ? 0.0 : par[0];
+        W.hi[k] = zero ? 0.0 : par[1];
         W.it[k] = 0;
-        W.st[k] = 0;
+        W.st[k] = zero;
     }
     int seq = 0;
     if (!bis_barrier(W.ctl, ++seq, err)) return;
@@ -338,7 +378,7 @@ __global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const
                 ++it;
             }
             int c = -1;
-            if (live && bis_step_test(lo, hi, it, rtol, atol, maxit, mid) == 0) c = sturm_chain(n, d, e2, mid, pivmin);
+            if (live && bis_step_test(lo, hi, it, rtol, atol, maxit, mid) == 0) c = sturm_chain(n, d, e2, mid, sc);
             W.cnt[w] = c;
         }
         if (!bis_barrier(W.ctl, ++seq, err)) return;
@@ -372,13 +412,14 @@ __global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const
         }
         if (!bis_barrier(W.ctl, ++seq, err)) return;
     }
-    for (int k = gtid; k < n; k += gthreads) eigs[k] = __dmul_rn(0.5, __dadd_rn(W.lo[k], W.hi[k]));
+    const double up = par[4];
+    for (int k = gtid; k < n; k += gthreads) eigs[k] = __dmul_rn(__dmul_rn(0.5, __dadd_rn(W.lo[k], W.hi[k])), up);
 }
 
 size_t bisect_workspace(int n) {
     Carver c(nullptr);
     c.take<double>((size_t)n + 1);
-    c.take<double>(4);
+    c.take<double>(8);
     c.take<double>((size_t)n);
     c.take<double>((size_t)n);
     for (int a = 0; a < 4; ++a) c.take<int>((size_t)n);
@@ -393,7 +434,7 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     if (ws_bytes < bisect_workspace(n)) return SEV_ERR_WORKSPACE;
     Carver c(ws);
     double *e2 = c.take<double>((size_t)n + 1);
-    double *par = c.take<double>(4);
+    double *par = c.take<double>(8);
     BisWs W;
     W.lo = c.take<double>((size_t)n);
     W.hi = c.take<double>((size_t)n);
@@ -414,13 +455,12 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     int per_sm = 0;
     SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bisect_rounds_kernel, kBisThreads, 0));
     if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
-    // A Sturm step is a chain of dependent FP64 operations (~1000 cycles on
-    // GB300); about 146 chains per SM cover that latency with the FP64 pipe
-    // busy (measured: ~44 G steps/s at saturation, 7.7 ms per 16384-step
-    // chain alone).  Rounds are sized to that budget; 1024 threads per CTA
-    // run a round of up to 150K chains in a single pass.
+    // A Sturm step has one FMA on its dependence chain and three FP64
+    // instructions in all; about 64 chains per SM keep the FP64 pipe busy
+    // through that latency.  Rounds are sized to that budget; 1024 threads
+    // per CTA run a round of up to 150K chains in a single pass.
     const int grid = h->sm_count;
-    int budget = grid * 146;
+    int budget = grid * 64;
     int maxit = 200;
     void *args[] = {(void *)&n, (void *)&d, (void *)&e2, (void *)&par, (void *)&rtol, (void *)&maxit,
                     (void *)&budget, (void *)&eigs, (void *)&W, (void *)&h->d_err};
@@ -434,8 +474,8 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
 
 // ------------------------------------------------- allocation-free variant
 // sev_tridiag_bisect_static: the same two kernels as sev_tridiag_bisect, but
-// their scratch (the squared off-diagonal, the Gershgorin/pivmin parameters
-// and an unused status slot) lives in this file-scope device array instead
+// their scratch (the squared scaled off-diagonal, the scaling and Gershgorin
+// parameters and an unused status slot) lives in this file-scope device array instead
 // of handle workspace, so a call allocates nothing.  The array is
 // (kStaticMaxN + 8) doubles (~512 KiB) on every device that loads the
 // library, held until the process exits.
@@ -473,9 +513,9 @@ extern "C" int sev_tridiag_bisect_static(int n, const double *d, const double *e
         S.ptr = (double *)p;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    double *e2 = S.ptr;                   // n + 1 doubles
-    double *par = S.ptr + kStaticMaxN + 2;  // 4 doubles
-    int *status = (int *)(S.ptr + kStaticMaxN + 6);
+    double *e2 = S.ptr;                     // n + 1 doubles
+    double *par = S.ptr + kStaticMaxN + 1;  // 6 doubles
+    int *status = (int *)(S.ptr + kStaticMaxN + 7);
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SEV_ERR_CUDA;
     bisect_prep_kernel<<<1, 1024, 0, st>>>(n, d, n > 1 ? e : d, e2, par);
     if (cudaGetLastError() != cudaSuccess) return SEV_ERR_CUDA;

@@ -366,3 +366,43 @@ def test_inertia_lapack_counts(orc):
     assert orc.inertia_lapack(K, 0.0) == 5
     assert orc.inertia_lapack(K, -2.0) == 0
     assert orc.inertia_lapack(K, 2.0) == 10
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 10, 257])
+def test_sturm_minors_equals_pivot_count(orc, n):
+    """The minors count (Sturm's theorem) and the LDL^T pivot count agree
+    with the eigenvalue count of the dense matrix at shifts inside gaps."""
+    d, e = I.random_tridiagonal(n, 11000 + n)
+    T = np.diag(d) + (np.diag(e, -1) + np.diag(e, 1) if n > 1 else 0.0)
+    lam = np.linalg.eigvalsh(T)
+    xs = [lam[0] - 1.0, lam[-1] + 1.0] + [0.5 * (lam[k] + lam[k + 1]) for k in range(n - 1)][:: max(1, n // 9)]
+    for x in xs:
+        want = int((lam < x).sum())
+        assert orc.sturm_count_minors(d, e, x) == want
+        assert orc.sturm_count(d, e, x) == want
+
+
+def test_sturm_minors_extreme_scales_and_zero(orc):
+    d, e = I.random_tridiagonal(400, 11100)
+    xs = [-3.0, -0.7, 0.0, 0.4, 2.9]
+    base = [orc.sturm_count_minors(d, e, x) for x in xs]
+    for k in (-600, -300, 300, 600):  # exact power-of-two scalings: no overflow, same counts
+        s = 2.0 ** k
+        assert [orc.sturm_count_minors(d * s, e * s, x * s) for x in xs] == base
+    z = np.zeros(50)
+    # x exactly at an eigenvalue: a zero minor counts as a sign change, as a
+    # zero pivot counts as negative under the pivmin rule
+    assert orc.sturm_count_minors(z, z[:49], 0.0) == orc.sturm_count(z, z[:49], 0.0) == 50
+    assert orc.sturm_count_minors(z, z[:49], 1.0) == 50
+    assert orc.sturm_count_minors(z, z[:49], -1.0) == 0
+    np.testing.assert_array_equal(orc.bisect(z, z[:49], 1e-14), z)  # T = 0: every eigenvalue exactly 0
+
+
+def test_bisect_power_of_two_scale_invariance(orc):
+    """The bisection runs on the exactly rescaled matrix, so scaling T by
+    2^k scales every computed eigenvalue by exactly 2^k."""
+    d, e = I.random_tridiagonal(150, 11200)
+    ref = orc.bisect(d, e, 1e-14)
+    for k in (-400, -7, 5, 400):
+        s = 2.0 ** k
+        np.testing.assert_array_equal(orc.bisect(d * s, e * s, 1e-14), ref * s)
