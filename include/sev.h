@@ -216,6 +216,17 @@ int sev_batch_autotune(sev_handle handle, int count, const int *n, int prec, int
 int sev_band_tridiag_extract(sev_handle handle, int n, const void *AB, int ldab, int prec, double *d,
                              double *e);
 
+/*
+ * Self-check of the mixed form's Householder scalars (no counterpart in the
+ * paper).  For count inputs alpha[i] (the leading entry, float) and the sum
+ * of squares of the rest as an unevaluated pair ssq_hi[i] + ssq_lo[i]
+ * (device floats), writes (tau, beta, 1/(alpha - beta)) as evaluated by the
+ * library's pair-float routine to out_pairfloat[3i..3i+2] and as evaluated
+ * in FP64 and rounded to float to out_fp64[3i..3i+2] (device), on `stream`.
+ */
+int sev_diag_house_scalars(int count, const float *alpha, const float *ssq_hi, const float *ssq_lo,
+                           float *out_pairfloat, float *out_fp64, void *stream);
+
 /* Synchronise the handle's stream and return (and clear) the first error
  * latched by device code since the last call, or SEV_OK. */
 int sev_get_error(sev_handle handle);

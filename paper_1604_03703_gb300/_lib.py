@@ -55,6 +55,7 @@ SIGNATURES = {
     "sev_eigvalsh_batched": (_i, [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_vp), _i, _i,
                                   ctypes.POINTER(_vp)]),
     "sev_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
+    "sev_diag_house_scalars": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None

@@ -40,32 +40,34 @@ struct TriWin {
     __device__ __forceinline__ T &sym(int u, int q) const { return u >= q ? at(u, q) : at(q, u); }
 };
 
-// Reflector scalars from this lane's x (lanes t < nr hold x_t): pair-float
-// sum of squares over the B-lane group, FP64 scalars computed by every lane
-// (no divergence; an FP64 instruction costs the same for 1 or 32 lanes).
+// Reflector scalars from this lane's x (lanes t < nr hold x_t), computed by
+// every lane (no divergence): FP32 data -- pair-float sum of squares over the
+// B-lane group and pair-float scalars (house_scalars_f2); FP64 data -- FP64.
 template <typename T, int B>
 __device__ __forceinline__ void tri_reflector(T x, int nr, T &v, T &tau, T &beta) {
     constexpr int W = B < 32 ? B : 32;
     const int lane = threadIdx.x & 31;
-    double ssq;
-    if (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4) {
         F2 acc{0.f, 0.f};
         if (lane >= 1 && lane < nr) f2_add_sq(acc, (float)x);
         acc = warp_sum_f2<W>(acc);
-        ssq = (double)acc.hi + (double)acc.lo;
+        float tf, bf, inf;
+        house_scalars_f2(__shfl_sync(0xffffffffu, (float)x, 0), acc, &tf, &bf, &inf);
+        tau = (T)tf;
+        beta = (T)bf;
+        v = lane == 0 ? T(1) : (lane < nr ? x * (T)inf : T(0));
     } else {
         const double xd = (lane >= 1 && lane < nr) ? (double)x : 0.0;
         double a = xd * xd;
 #pragma unroll
         for (int off = W / 2; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
-        ssq = a;
+        const double alpha = (double)__shfl_sync(0xffffffffu, x, 0);
+        double td, bd, id;
+        house_scalars(alpha, a, &td, &bd, &id);
+        tau = (T)td;
+        beta = (T)bd;
+        v = lane == 0 ? T(1) : (lane < nr ? x * (T)id : T(0));
     }
-    const double alpha = (double)__shfl_sync(0xffffffffu, x, 0);
-    double td, bd, id;
-    house_scalars(alpha, ssq, &td, &bd, &id);
-    tau = (T)td;
-    beta = (T)bd;
-    v = lane == 0 ? T(1) : (lane < nr ? x * (T)id : T(0));
 }
 
 // One chase (i, j), h = 1, by one warp on the shared window, with the rows a

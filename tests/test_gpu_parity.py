@@ -256,3 +256,29 @@ def test_argument_errors(H, torch_cuda):
     assert ei.value.code == -6
     with pytest.raises(SevError):
         H.tridiag_bisect(A[0], A[0][:7], -1.0)
+
+
+def test_pairfloat_house_scalars_equal_fp64_rounded(H, torch_cuda):
+    """The mixed form evaluates tau, beta and 1/(alpha - beta) in pair-float
+    arithmetic; on inputs over many decades (and zero vectors) the FP32
+    results equal the FP64 evaluation rounded to FP32."""
+    import ctypes
+
+    torch = torch_cuda
+    r = I.rng(12000)
+    m = 1 << 18
+    alpha = (r.uniform(-0.5, 0.5, m) * 10.0 ** r.integers(-6, 7, m)).astype(np.float32)
+    ssq = r.uniform(0, 1, m) * 10.0 ** r.integers(-12, 13, m)
+    ssq[::97] = 0.0
+    hi = ssq.astype(np.float32)
+    lo = (ssq - hi.astype(np.float64)).astype(np.float32)
+    a_t, h_t, l_t = (torch.from_numpy(v).cuda() for v in (alpha, hi, lo))
+    o1 = torch.empty(3 * m, dtype=torch.float32, device="cuda")
+    o2 = torch.empty_like(o1)
+    s = torch.cuda.current_stream().cuda_stream
+    rc = H._lib.sev_diag_house_scalars(m, ctypes.c_void_p(a_t.data_ptr()), ctypes.c_void_p(h_t.data_ptr()),
+                                       ctypes.c_void_p(l_t.data_ptr()), ctypes.c_void_p(o1.data_ptr()),
+                                       ctypes.c_void_p(o2.data_ptr()), ctypes.c_void_p(s))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert torch.equal(o1, o2)
