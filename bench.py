@@ -42,6 +42,7 @@ def parse():
     p.add_argument("--b0", type=int, default=128)
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-form timing")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return p.parse_args()
 
@@ -287,6 +288,93 @@ def gen_workload(n, device):
     return A64, D
 
 
+def time_plan(plan, work, orig, reps=3):
+    """Device time of plan.run() (CUDA events), best of reps; the inputs are
+    restored before every run, outside the events."""
+    import torch
+
+    best = None
+    for _ in range(reps):
+        for w, o in zip(work, orig):
+            w.copy_(o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return best
+
+
+def max_over_ranks(ms, world, device):
+    if world == 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def bench_batched(h, device, args, rank=0, world=1):
+    """The two batched workloads, FP64 and mixed: matrices per second of one
+    plan run (one persistent launch for the small matrices; the SCF-like
+    orders run the single-matrix path one after another).  With N ranks each
+    takes its LPT shard of the batch (no data-path collective); the time is
+    the slowest rank's."""
+    import torch
+
+    from paper_1604_03703_gb300 import _lib
+    from paper_1604_03703_gb300 import inputs as I
+    from paper_1604_03703_gb300 import shard
+
+    out = {}
+    host_all = I.batch_small()
+    part = shard.lpt_partition([A.shape[0] for A in host_all], world)[rank]
+    host = [host_all[i] for i in part]
+    del host_all
+    sizes = [A.shape[0] for A in host]
+    small = {"workload": "4096 symmetric N(0,1)/sqrt(n) matrices, n uniform in 32..512", "count": 4096,
+             "sharding": "lpt over %d rank(s)" % world}
+    for name, dt, prec in (("mixed", torch.float32, _lib.SEV_MIXED), ("fp64", torch.float64, _lib.SEV_FP64)):
+        b = h.batch_autotune(sizes, prec)
+        orig = [torch.from_numpy(A).to(dt).to(device) for A in host]
+        work = [t.clone() for t in orig]
+        outs = [torch.empty(t.shape[0], dtype=torch.float64, device=device) for t in orig]
+        plan = h.batch_plan(work, outs, b)
+        ms = max_over_ranks(time_plan(plan, work, orig), world, device)
+        h.raise_device_error("batched " + name)
+        plan.close()
+        small[name] = {"ms": ms, "mats_per_s": 4096 / (ms / 1e3), "b": b, "launches": 1}
+        del orig, work, outs
+        torch.cuda.empty_cache()
+    small["mixed_speedup"] = small["fp64"]["ms"] / small["mixed"]["ms"]
+    out["small"] = small
+    scf = {"workload": "64 SCF-like matrices A0(n) + 1e-3 E, n uniform in 1024..6144, D uniform in [-10, 10]",
+           "count": 64}
+    part = shard.lpt_partition([int(m) for m in I.batch_sizes(64, 1024, 6144, I.SEED_BASE + 4)], world)[rank]
+    mats = [A for k, A in enumerate(I.batch_scf_torch(64, device=device)) if k in set(part)]
+    for name, dt in (("mixed", torch.float32), ("fp64", torch.float64)):
+        orig = [A.to(dt) for A in mats]
+        work = [t.clone() for t in orig]
+        outs = [torch.empty(t.shape[0], dtype=torch.float64, device=device) for t in orig]
+        plan = h.batch_plan(work, outs, 0)
+        ms = max_over_ranks(time_plan(plan, work, orig, reps=1), world, device)
+        h.raise_device_error("scf " + name)
+        plan.close()
+        scf[name] = {"ms": ms, "mats_per_s": 64 / (ms / 1e3)}
+        del orig, work, outs
+        torch.cuda.empty_cache()
+    scf["mixed_speedup"] = scf["fp64"]["ms"] / scf["mixed"]["ms"]
+    out["scf"] = scf
+    del mats
+    torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------- arms
 def run_reference(args):
     rank, world, local = dist_env()
@@ -434,6 +522,12 @@ def run_ours(args):
         fp64 = {"eigvalsh_s": f_ms / 1e3, "tflops": nominal_flops(n) / (f_ms / 1e3) / 1e12, "b0": 64,
                 "max_err_vs_D": f_err, "mixed_speedup": f_ms / ms_per_step}
 
+    batched = None
+    if not args.no_batched:
+        del A
+        torch.cuda.empty_cache()
+        batched = bench_batched(h, device, args, rank, world)
+
     peaks = measured_peaks()
     amount, unit, bound = kernel_model(dominant, n, b0, 4)
     dom_ms_step = dom_ms / args.steps if dom_ms else prof[dominant][0]
@@ -464,6 +558,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clk,
         "fp64": fp64,
+        "batched": batched,
         "kernels_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
     }
     if rank == 0:

@@ -529,6 +529,98 @@ __device__ void cta_gemm(int M, int N, int K, T alpha, const T *A, int lda, cons
     }
 }
 
+// --------------------------------------------------- blocked (level-3) QR
+// Householder QR of the m x nc block P in panels of kQrNB columns: each
+// panel is factorised column by column (cta_qr, reflectors applied inside
+// the panel only), its compact-WY factor T_j formed (cta_form_t), and the
+// trailing columns updated at once, C <- (I - V T_j^T V^T) C = C - V (T_j^T
+// (V^T C)), as two shared-memory GEMMs -- each trailing element is read and
+// written twice per panel instead of twice per reflector.  The reflectors
+// and the result are those of cta_qr up to rounding.  T_j (upper, jb x jb)
+// is left in Tblk at columns [j0, j0 + jb) (an kQrNB x nc array, ld kQrNB).
+// Scratch: Wk (kQrNB x nc), Gb (kQrNB x kQrNB).  Returns r = min(nc, m-1).
+constexpr int kQrNB = 32;
+
+template <typename T>
+__device__ int cta_qr_blocked(int m, int nc, T *P, int ld, T *tau, T *Tblk, T *Wk, T *Gb) {
+    const int r = nc < m - 1 ? nc : m - 1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (r <= 0) {
+        __syncthreads();
+        return r < 0 ? 0 : r;
+    }
+    for (int j0 = 0; j0 < r; j0 += kQrNB) {
+        const int jb = r - j0 < kQrNB ? r - j0 : kQrNB;
+        T *Pj = P + j0 + (size_t)j0 * ld;
+        const int mj = m - j0;
+        const int rj = cta_qr(mj, jb, Pj, ld, tau + j0, nullptr);  // = jb: j0 + jb <= r <= m - 1
+        T *Tj = Tblk + (size_t)j0 * kQrNB;
+        cta_form_t(mj, rj, Pj, ld, tau + j0, Tj, kQrNB, Gb, kQrNB);
+        const int nct = nc - j0 - jb;
+        if (nct <= 0) continue;
+        T *C = Pj + (size_t)jb * ld;
+        // V explicit in place (unit diagonal, zeros above); R's triangle saved in Gb
+        for (int idx = tid; idx < jb * jb; idx += nt) {
+            const int i = idx % jb, c = idx / jb;
+            if (i <= c) {
+                Gb[i + (size_t)c * kQrNB] = Pj[i + (size_t)c * ld];
+                Pj[i + (size_t)c * ld] = i == c ? T(1) : T(0);
+            }
+        }
+        __syncthreads();
+        cta_gemm<T, true, false>(jb, nct, mj, T(1), Pj, ld, C, ld, T(0), Wk, kQrNB);  // W = V^T C
+        __syncthreads();
+        for (int c = tid; c < nct; c += nt) {  // W <- T^T W, bottom row first (in place)
+            T *w = Wk + (size_t)c * kQrNB;
+            for (int i = jb - 1; i >= 0; --i) {
+                T acc = 0;
+                for (int q = 0; q <= i; ++q) acc += Tj[q + (size_t)i * kQrNB] * w[q];
+                w[i] = acc;
+            }
+        }
+        __syncthreads();
+        cta_gemm<T, false, false>(mj, nct, jb, T(-1), Pj, ld, Wk, kQrNB, T(1), C, ld);  // C -= V W
+        __syncthreads();
+        for (int idx = tid; idx < jb * jb; idx += nt) {
+            const int i = idx % jb, c = idx / jb;
+            if (i <= c) Pj[i + (size_t)c * ld] = Gb[i + (size_t)c * kQrNB];
+        }
+        __syncthreads();
+    }
+    return r;
+}
+
+// M (rows x w, ld) <- H_0 H_1 ... H_{nr-1} M with the reflectors held
+// explicitly (unit lower trapezoidal) in Y (rows x nr, ld) and the blocked
+// compact-WY factors of cta_qr_blocked in Tblk: block by block from the
+// last, M <- M - V (T_j (V^T M)).  Scratch Wk (kQrNB x w).
+template <typename T>
+__device__ void cta_apply_blocked(int rows, int w, int nr, const T *Y, int ld, const T *Tblk, T *M, T *Wk) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nblk = (nr + kQrNB - 1) / kQrNB;
+    for (int jbk = nblk - 1; jbk >= 0; --jbk) {
+        const int j0 = jbk * kQrNB;
+        const int jb = nr - j0 < kQrNB ? nr - j0 : kQrNB;
+        const T *V = Y + j0 + (size_t)j0 * ld;
+        const T *Tj = Tblk + (size_t)j0 * kQrNB;
+        T *Mj = M + j0;
+        const int mj = rows - j0;
+        cta_gemm<T, true, false>(jb, w, mj, T(1), V, ld, Mj, ld, T(0), Wk, kQrNB);  // W = V^T M
+        __syncthreads();
+        for (int c = tid; c < w; c += nt) {  // W <- T W, top row first (in place)
+            T *wc = Wk + (size_t)c * kQrNB;
+            for (int i = 0; i < jb; ++i) {
+                T acc = 0;
+                for (int q = i; q < jb; ++q) acc += Tj[i + (size_t)q * kQrNB] * wc[q];
+                wc[i] = acc;
+            }
+        }
+        __syncthreads();
+        cta_gemm<T, false, false>(mj, w, jb, T(-1), V, ld, Wk, kQrNB, T(1), Mj, ld);  // M -= V W
+        __syncthreads();
+    }
+}
+
 // --------------------------------------------------- batched global copies
 // Copy `count` elements, element k read by src(k) (a global load) and written
 // by dst(k, v), with U independent loads in flight per thread before any of

@@ -5,12 +5,14 @@
 //
 // Tree QR.  The panel's rows are split into L leaves of at least r_leaf rows
 // (the last leaf takes the remainder).  Leaf l is QR'd in one CTA:
-// A_l = W_l R_l.  Going up, a node stacks the R's of its (up to F) children
+// A_l = W_l R_l (blocked Householder QR, cta_qr_blocked, keeping the
+// compact-WY factor of every 32-column block for the way down).  Going up, a node stacks the R's of its (up to F) children
 // and QRs the stack: [R_c0; ...; R_ck] = Z R.  Going down (Algorithm 3.2's
 // Q_i = W_i Z_i), a node's Z block is pushed through its reflectors,
 // [Z; 0] -> H [Z; 0], and the row blocks of the result are its children's
 // Z blocks; at a leaf, Q_l = H_l [Z_l; 0] gives the rows of the explicit
-// thin Q.  The root's Z is the identity.
+// thin Q.  The root's Z is the identity.  Both pushes apply the reflectors
+// a block at a time, M <- M - V (T (V^T M)) (cta_apply_blocked).
 //
 // Reconstruction (Cor. 3.7).  Q1 - S = U1 W1 (unpivoted LU, U1 unit lower,
 // W1 upper) with S a diagonal sign matrix chosen during the LU: at step k,
@@ -36,18 +38,23 @@ struct TreePlan {
     size_t ynode_stride = 0;   // elements per internal-node Y slot (F b x b)
 };
 
-static int col_slices(int b) { return (b >= 64 && b % 2 == 0) ? 2 : 1; }
+static int col_slices(int b) { return b >= 64 && b % 32 == 0 ? b / 32 : 1; }  // apply slices of 32 columns
 
-// Rows per leaf: the leaf apply holds Y (2 r_leaf rows x b) and a column
-// slice of M (2 r_leaf rows x b/cs) in shared memory; leaves need >= b rows.
+template <typename T>
+static size_t smem_leaf_qr(int r_leaf, int b);
+template <typename T>
+static size_t smem_leaf_apply(int r_leaf, int b, int cs);
+
+// Rows per leaf: the largest multiple of 32 (>= b, <= 1024) whose leaf QR
+// and leaf apply both fit the shared-memory budget.
 template <typename T>
 static int pick_r_leaf(int b, size_t budget) {
-    const size_t w = (size_t)b / col_slices(b);
-    long r = (long)((budget / sizeof(T) - b) / ((size_t)b + w) / 2) - 1;
-    r &= ~31L;
-    if (r > 1024) r = 1024;
-    if (r < b) r = b;
-    return (int)r;
+    int best = b;
+    for (int r = 32; r <= 1024; r += 32) {
+        if (r < b) continue;
+        if (smem_leaf_qr<T>(r, b) <= budget && smem_leaf_apply<T>(r, b, col_slices(b)) <= budget) best = r;
+    }
+    return best;
 }
 
 static void make_plan(TreePlan &p, int N, int b, int r_leaf, int F) {
@@ -83,7 +90,8 @@ __host__ __device__ __forceinline__ int leaf_rows(int N, int r_leaf, int L, int 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     tsqr_leaf_qr_kernel(const T *__restrict__ P, int ldp, int N, int b, int r_leaf, int L, T *__restrict__ Yleaf,
-                        int ldy, T *__restrict__ tau, int *__restrict__ nref, T *__restrict__ Rbuf) {
+                        int ldy, T *__restrict__ tau, int *__restrict__ nref, T *__restrict__ Rbuf,
+                        T *__restrict__ Tbuf) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int l = blockIdx.x;
     const int row0 = l * r_leaf;
@@ -91,18 +99,21 @@ __global__ void __launch_bounds__(kThreads)
     const int ld = (2 * r_leaf) | 1;
     T *S = (T *)smem;
     T *tl = S + (size_t)ld * b;
-    double *red = (double *)(((uintptr_t)(tl + b) + 15) & ~(uintptr_t)15);
+    T *Tblk = tl + b;
+    T *Wk = Tblk + (size_t)kQrNB * b;
+    T *Gb = Wk + (size_t)kQrNB * b;
     batched_copy<T>(
         rows * b, threadIdx.x, blockDim.x, [&](int k) { return P[(size_t)(row0 + k % rows) + (size_t)(k / rows) * ldp]; },
         [&](int k, T v) { S[k % rows + (size_t)(k / rows) * ld] = v; });
     __syncthreads();
-    const int r = cta_qr(rows, b, S, ld, tl, red);
+    const int r = cta_qr_blocked(rows, b, S, ld, tl, Tblk, Wk, Gb);
     for (int idx = threadIdx.x; idx < rows * b; idx += blockDim.x) {
         const int i = idx % rows, c = idx / rows;
         T v = 0;
         if (c < r) v = (i < c) ? T(0) : (i == c ? T(1) : S[i + (size_t)c * ld]);
         Yleaf[(size_t)(row0 + i) + (size_t)c * ldy] = v;
     }
+    for (int idx = threadIdx.x; idx < kQrNB * b; idx += blockDim.x) Tbuf[(size_t)l * kQrNB * b + idx] = Tblk[idx];
     T *R = Rbuf + (size_t)l * b * b;
     for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
         const int i = idx % b, c = idx / b;
@@ -116,7 +127,8 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
     tsqr_node_qr_kernel(int b, int F, int cnt_child, int off_child, int off_node, T *__restrict__ Rbuf,
-                        T *__restrict__ Ynode, size_t ynode_stride, T *__restrict__ tau, int *__restrict__ nref) {
+                        T *__restrict__ Ynode, size_t ynode_stride, T *__restrict__ tau, int *__restrict__ nref,
+                        T *__restrict__ Tbuf) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int p = blockIdx.x;
     const int c0 = F * p, c1 = min(F * p + F, cnt_child);
@@ -133,7 +145,9 @@ __global__ void __launch_bounds__(kThreads)
     const int ld = (F * b) | 1;
     T *S = (T *)smem;
     T *tl = S + (size_t)ld * b;
-    double *red = (double *)(((uintptr_t)(tl + b) + 15) & ~(uintptr_t)15);
+    T *Tblk = tl + b;
+    T *Wk = Tblk + (size_t)kQrNB * b;
+    T *Gb = Wk + (size_t)kQrNB * b;
     batched_copy<T>(
         rows * b, threadIdx.x, blockDim.x,
         [&](int k) {
@@ -142,8 +156,9 @@ __global__ void __launch_bounds__(kThreads)
         },
         [&](int k, T v) { S[k % rows + (size_t)(k / rows) * ld] = v; });
     __syncthreads();
-    const int r = cta_qr(rows, b, S, ld, tl, red);
+    const int r = cta_qr_blocked(rows, b, S, ld, tl, Tblk, Wk, Gb);
     T *Y = Ynode + (size_t)p * ynode_stride;
+    for (int idx = threadIdx.x; idx < kQrNB * b; idx += blockDim.x) Tbuf[(size_t)node * kQrNB * b + idx] = Tblk[idx];
     for (int idx = threadIdx.x; idx < rows * b; idx += blockDim.x) {
         const int i = idx % rows, c = idx / rows;
         T v = 0;
@@ -159,24 +174,6 @@ __global__ void __launch_bounds__(kThreads)
 }
 
 // ------------------------------------------------------- apply kernels (down)
-// M (rows x w, shared, ld) <- H_0 H_1 ... H_{nr-1} M with the reflectors
-// stored explicitly in Y (shared, rows x b, ld) and tau.
-template <typename T>
-__device__ void cta_apply_reflectors(int rows, int w, int nr, const T *Y, int ld, const T *tl, T *M) {
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int k = nr - 1; k >= 0; --k) {
-        const T *v = Y + (size_t)k * ld;
-        const T tk = tl[k];
-        for (int c = warp; c < w; c += 4 * nw) {
-            T *c1 = (c + nw < w) ? M + (size_t)(c + nw) * ld : (T *)nullptr;
-            T *c2 = (c + 2 * nw < w) ? M + (size_t)(c + 2 * nw) * ld : (T *)nullptr;
-            T *c3 = (c + 3 * nw < w) ? M + (size_t)(c + 3 * nw) * ld : (T *)nullptr;
-            warp_apply4(rows, k, v, tk, M + (size_t)c * ld, c1, c2, c3);
-        }
-        __syncthreads();
-    }
-}
-
 // Node level: CTA (p, slice) pushes the node's Z (columns of the slice)
 // through its reflectors and scatters the row blocks to the children's Z.
 // Z_root (lev = top) is the identity when root_identity != 0.
@@ -184,7 +181,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     tsqr_node_apply_kernel(int b, int F, int cs, int cnt_child, int off_child, int off_node, const T *__restrict__ Ynode,
                            size_t ynode_stride, const T *__restrict__ tau, const int *__restrict__ nref,
-                           T *__restrict__ Zbuf, int root_identity) {
+                           T *__restrict__ Zbuf, int root_identity, const T *__restrict__ Tbuf) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int p = blockIdx.x, slice = blockIdx.y;
     const int w = b / cs, col0 = slice * w;
@@ -197,6 +194,8 @@ __global__ void __launch_bounds__(kThreads)
     T *Ys = (T *)smem;
     T *Ms = Ys + (size_t)ld * b;
     T *tl = Ms + (size_t)ld * w;
+    T *Tblk = tl + b;
+    T *Wk = Tblk + (size_t)kQrNB * b;
     const int nr = nref[node];
     batched_copy<T>(
         rows * w, threadIdx.x, blockDim.x,
@@ -212,10 +211,11 @@ __global__ void __launch_bounds__(kThreads)
         batched_copy<T>(
             rows * nr, threadIdx.x, blockDim.x, [&](int k) { return Y[k]; },
             [&](int k, T v) { Ys[k % rows + (size_t)(k / rows) * ld] = v; });
-        for (int c = threadIdx.x; c < nr; c += blockDim.x) tl[c] = tau[(size_t)node * b + c];
+        for (int idx = threadIdx.x; idx < kQrNB * nr; idx += blockDim.x)
+            Tblk[idx] = Tbuf[(size_t)node * kQrNB * b + idx];
     }
     __syncthreads();
-    if (nr > 0) cta_apply_reflectors(rows, w, nr, Ys, ld, tl, Ms);
+    if (nr > 0) cta_apply_blocked(rows, w, nr, Ys, ld, Tblk, Ms, Wk);
     for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
         const int r = idx % rows, c = idx / rows;
         const int k = r / b, rr = r % b;
@@ -228,7 +228,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     tsqr_leaf_apply_kernel(int N, int b, int r_leaf, int L, int cs, const T *__restrict__ Yleaf, int ldy,
                            const T *__restrict__ tau, const int *__restrict__ nref, const T *__restrict__ Zbuf,
-                           T *__restrict__ Q, int ldq) {
+                           T *__restrict__ Q, int ldq, const T *__restrict__ Tbuf) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int l = blockIdx.x, slice = blockIdx.y;
     const int w = b / cs, col0 = slice * w;
@@ -238,6 +238,8 @@ __global__ void __launch_bounds__(kThreads)
     T *Ys = (T *)smem;
     T *Ms = Ys + (size_t)ld * b;
     T *tl = Ms + (size_t)ld * w;
+    T *Tblk = tl + b;
+    T *Wk = Tblk + (size_t)kQrNB * b;
     const int nr = nref[l];
     const T *Zl = Zbuf + (size_t)l * b * b;
     batched_copy<T>(
@@ -251,9 +253,9 @@ __global__ void __launch_bounds__(kThreads)
         rows * nr, threadIdx.x, blockDim.x,
         [&](int k) { return Yleaf[(size_t)(row0 + k % rows) + (size_t)(k / rows) * ldy]; },
         [&](int k, T v) { Ys[k % rows + (size_t)(k / rows) * ld] = v; });
-    for (int c = threadIdx.x; c < nr; c += blockDim.x) tl[c] = tau[(size_t)l * b + c];
+    for (int idx = threadIdx.x; idx < kQrNB * nr; idx += blockDim.x) Tblk[idx] = Tbuf[(size_t)l * kQrNB * b + idx];
     __syncthreads();
-    cta_apply_reflectors(rows, w, nr, Ys, ld, tl, Ms);
+    cta_apply_blocked(rows, w, nr, Ys, ld, Tblk, Ms, Wk);
     for (int idx = threadIdx.x; idx < rows * w; idx += blockDim.x) {
         const int r = idx % rows, c = idx / rows;
         Q[(size_t)(row0 + r) + (size_t)(col0 + c) * ldq] = Ms[r + (size_t)c * ld];
@@ -412,21 +414,24 @@ __global__ void __launch_bounds__(kThreads)
 // ---------------------------------------------------------------- driver
 template <typename T>
 static size_t smem_leaf_qr(int r_leaf, int b) {
-    return sizeof(T) * ((size_t)((2 * r_leaf) | 1) * b + b) + 16 + 32 * sizeof(double);
+    // block, tau, T blocks, GEMM scratch, R save, reduction scratch
+    return sizeof(T) * ((size_t)((2 * r_leaf) | 1) * b + b + 2 * (size_t)kQrNB * b + kQrNB * kQrNB) + 16 +
+           32 * sizeof(double);
 }
 template <typename T>
 static size_t smem_node_qr(int F, int b) {
-    return sizeof(T) * ((size_t)((F * b) | 1) * b + b) + 16 + 32 * sizeof(double);
+    return sizeof(T) * ((size_t)((F * b) | 1) * b + b + 2 * (size_t)kQrNB * b + kQrNB * kQrNB) + 16 +
+           32 * sizeof(double);
 }
 template <typename T>
 static size_t smem_leaf_apply(int r_leaf, int b, int cs) {
-    const size_t ld = (2 * r_leaf) | 1;
-    return sizeof(T) * (ld * b + ld * (b / cs) + b);
+    const size_t ld = (2 * r_leaf) | 1, w = b / cs;
+    return sizeof(T) * (ld * b + ld * w + b + (size_t)kQrNB * b + kQrNB * w);
 }
 template <typename T>
 static size_t smem_node_apply(int F, int b, int cs) {
-    const size_t ld = (F * b) | 1;
-    return sizeof(T) * (ld * b + ld * (b / cs) + b);
+    const size_t ld = (F * b) | 1, w = b / cs;
+    return sizeof(T) * (ld * b + ld * w + b + (size_t)kQrNB * b + kQrNB * w);
 }
 
 struct PanelWs {
@@ -435,7 +440,7 @@ struct PanelWs {
 
 template <typename T>
 struct PanelBuffers {
-    T *Yleaf, *Ynode, *tau, *Rbuf, *Zbuf, *Q, *Winv;
+    T *Yleaf, *Ynode, *tau, *Rbuf, *Zbuf, *Q, *Winv, *Tbuf;
     int *nref;
 };
 
@@ -450,6 +455,7 @@ static void carve_panel(Carver &c, PanelBuffers<T> &B, int n, int b, int r_leaf,
     B.Zbuf = c.take<T>((size_t)nodes * b * b);
     B.Q = c.take<T>((size_t)n * b);
     B.Winv = c.take<T>((size_t)b * b);
+    B.Tbuf = c.take<T>((size_t)nodes * kQrNB * b);
     B.nref = c.take<int>((size_t)nodes);
 }
 
@@ -488,7 +494,7 @@ int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws)
     if (plan.L == 1) {
         // single leaf: Householder QR of the whole panel gives (U, T) directly
         SEV_LAUNCH(h, K_TSQR_LEAF, tsqr_leaf_qr_kernel<T>, 1, kThreads, s_leaf, P, lda, N, b, r_leaf, 1, U, N, B.tau,
-                   B.nref, B.Rbuf);
+                   B.nref, B.Rbuf, B.Tbuf);
         const size_t s_fin = sizeof(T) * 2 * (size_t)(b + 1) * b;
         SEV_CUDA(cudaFuncSetAttribute(single_leaf_finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)s_fin));
@@ -497,7 +503,7 @@ int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws)
         return SEV_OK;
     }
     SEV_LAUNCH(h, K_TSQR_LEAF, tsqr_leaf_qr_kernel<T>, plan.L, kThreads, s_leaf, P, lda, N, b, r_leaf, plan.L,
-               B.Yleaf, N, B.tau, B.nref, B.Rbuf);
+               B.Yleaf, N, B.tau, B.nref, B.Rbuf, B.Tbuf);
     // up the tree
     const size_t s_node = smem_node_qr<T>(F, b);
     SEV_CUDA(cudaFuncSetAttribute(tsqr_node_qr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_node));
@@ -507,7 +513,7 @@ int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws)
         // and the down-sweep needs every level, so give each level its own)
         T *Ylev = B.Ynode + (size_t)(plan.off[lev] - plan.L) * plan.ynode_stride;
         SEV_LAUNCH(h, K_TSQR_TREE, tsqr_node_qr_kernel<T>, plan.cnt[lev], kThreads, s_node, b, F, plan.cnt[lev - 1],
-                   plan.off[lev - 1], plan.off[lev], B.Rbuf, Ylev, plan.ynode_stride, B.tau, B.nref);
+                   plan.off[lev - 1], plan.off[lev], B.Rbuf, Ylev, plan.ynode_stride, B.tau, B.nref, B.Tbuf);
     }
     // down the tree
     const size_t s_napply = smem_node_apply<T>(F, b, cs);
@@ -518,13 +524,13 @@ int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws)
         dim3 grid(plan.cnt[lev], cs);
         SEV_LAUNCH(h, K_TSQR_DOWN, tsqr_node_apply_kernel<T>, grid, kThreads, s_napply, b, F, cs, plan.cnt[lev - 1],
                    plan.off[lev - 1], plan.off[lev], Ylev, plan.ynode_stride, B.tau, B.nref, B.Zbuf,
-                   lev == plan.nlev - 1 ? 1 : 0);
+                   lev == plan.nlev - 1 ? 1 : 0, B.Tbuf);
     }
     const size_t s_lapply = smem_leaf_apply<T>(r_leaf, b, cs);
     SEV_CUDA(
         cudaFuncSetAttribute(tsqr_leaf_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_lapply));
     SEV_LAUNCH(h, K_TSQR_LEAF_Q, tsqr_leaf_apply_kernel<T>, dim3(plan.L, cs), kThreads, s_lapply, N, b, r_leaf, plan.L,
-               cs, B.Yleaf, N, B.tau, B.nref, B.Zbuf, B.Q, N);
+               cs, B.Yleaf, N, B.tau, B.nref, B.Zbuf, B.Q, N, B.Tbuf);
     // reconstruction
     const T *Rroot = B.Rbuf + (size_t)(plan.total - 1) * b * b;
     const size_t s_lu = sizeof(T) * (2 * (size_t)(b + 1) * b + b);

@@ -203,3 +203,29 @@ def batch_scf(count: int = 64, seed: int = SEED_BASE + 4):
             base[m] = qdq(D, seed + 200000 + m)
         out.append(base[m] + 1e-3 * semicircle(m, seed + 1 + k))
     return out
+
+
+def batch_scf_torch(count: int = 64, seed: int = SEED_BASE + 4, device="cuda", dtype=None):
+    """batch_scf generated with torch on the GPU (the host QRs of orders up
+    to 6144 take minutes): orders from batch_sizes(count, 1024, 6144, seed);
+    per distinct order A0 = qdq_torch(D) with D uniform in [-10, 10] (numpy
+    stream seed + 100000 + n, Q from seed + 200000 + n); matrix k adds
+    1e-3 E_k, E_k symmetric N(0,1)/sqrt(n) from torch's stream seed + 1 + k."""
+    import torch
+
+    sizes = batch_sizes(count, 1024, 6144, seed)
+    base = {}
+    out = []
+    for k, m in enumerate(sizes):
+        m = int(m)
+        if m not in base:
+            D = rng(seed + 100000 + m).uniform(-10.0, 10.0, m)
+            base[m] = qdq_torch(D, seed + 200000 + m, device)
+        g = torch.Generator(device=device)
+        g.manual_seed(seed + 1 + k)
+        G = torch.randn(m, m, generator=g, device=device, dtype=torch.float64)
+        E = torch.tril(G)
+        E = (E + torch.tril(E, -1).T) / np.sqrt(m)
+        A = base[m] + 1e-3 * E
+        out.append(A if dtype is None else A.to(dtype))
+    return out
