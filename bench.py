@@ -5,7 +5,7 @@ Workload (default): n = 16384, mixed precision (FP32 data, tensor-core
 trailing update, FP64 Householder norms/tau/beta and FP64 Sturm recurrence),
 A = Q diag(D) Q^T with D geometrically spaced over 1e-6..1 in magnitude with
 random signs and 16-fold clusters of gap 1e-10, Q from the QR of a seeded
-N(0,1) matrix; first half-bandwidth b0 = 128, band schedule 128 -> 32 -> 1.
+N(0,1) matrix; first half-bandwidth b0 = 128, band schedule 128 -> 32 -> 16 -> 1.
 A step is one sev_eigvalsh call (full-to-band, every band-to-band stage,
 bisection).  The FP64 form of the same matrix is timed beside it.
 
@@ -134,18 +134,24 @@ def panel_sizes(n, b):
 
 
 def schedule(b0, elem=4):
-    """The library's band schedule: straight to 1 from b <= 32 (b <= 16 for
-    FP64), a wider band first to the widest such width dividing it."""
+    """The library's band schedule (see api.cu): b <= 16 -> 1, b >= 128 ->
+    32, other multiples of 16 -> 16, else the widest supported divisor."""
     def tri(b):
         return b in (2, 4, 8, 16) or (b == 32 and elem == 4)
     s = [b0]
     while s[-1] > 1:
         b = s[-1]
         nxt = 1 if b % 2 else b // 2
-        if tri(b):
+        if b <= 16 and tri(b):
+            nxt = 1
+        elif b >= 128 and b % 32 == 0:
+            nxt = 32
+        elif b > 16 and b % 16 == 0:
+            nxt = 16
+        elif tri(b):
             nxt = 1
         else:
-            w = 32
+            w = 16
             while w >= 2:
                 if tri(w) and b % w == 0 and w < b:
                     nxt = w
@@ -485,6 +491,24 @@ def run_ours(args):
     lam_np = lam.cpu().numpy()
     err = float(np.abs(np.sort(lam_np) - D).max() / Dmax)
 
+    # the library's own default band width (b0 = 0 picks 64 at this size), same matrix
+    auto = None
+    if rank == 0 or world > 1:
+        ea = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+        A.copy_(A0)
+        h.eigvalsh(A, 0, out=lam)
+        for e0, e1 in ea:
+            A.copy_(A0)
+            e0.record()
+            h.eigvalsh(A, 0, out=lam)
+            e1.record()
+        torch.cuda.synchronize()
+        h.raise_device_error("default b0")
+        a_ms = min(e0.elapsed_time(e1) for e0, e1 in ea)
+        a_err = float(np.abs(np.sort(lam.cpu().numpy()) - D).max() / Dmax)
+        auto = {"b0": 64, "schedule": schedule(64, 4), "ms_per_step": a_ms,
+                "tflops": nominal_flops(n) / (a_ms / 1e3) / 1e12, "max_err_vs_D": a_err}
+
     # end to end through the host-buffer entry point (H2D + solve + D2H)
     e2e = None
     if not args.no_e2e:
@@ -558,6 +582,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": clk,
         "fp64": fp64,
+        "default_b0": auto,
         "batched": batched,
         "kernels_ms_per_step": {k: round(v[0], 3) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
     }

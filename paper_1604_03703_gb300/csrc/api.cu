@@ -90,25 +90,34 @@ int get_workspace(sev_ctx *h, size_t bytes, void **out) {
 
 static int default_b0(int n, int prec) {
     if (prec == SEV_FP64) return n >= 4096 ? 64 : 32;
-    return n >= 12288 ? 128 : (n >= 1024 ? 64 : 32);
+    return n >= 1024 ? 64 : 32;  // 64 -> 16 -> 1 measured best at n = 16384 (1.25 s against 1.62 s for 128)
 }
 
 // Band schedule (Algorithm 4.3; the paper allows a reduction factor k > 2
-// per stage): a band the one-stage b -> 1 kernel supports goes straight to 1;
-// a wider band first goes to the widest such width that divides it (one
-// stage with k = b/32 for b0 = 128 -- the measured best on this part, since a
-// stage's critical path is ~3n/h chases of ~h reflector steps each) or, when
-// none divides it, is halved; an odd band finishes with b -> 1.
+// per stage).  Measured on GB300 at n = 16384 (FP32): the one-stage b -> 1
+// kernel is fastest from b = 16 (192 ms, against 366 ms from 32), a
+// 32 -> 16 stage costs 139 ms, 64 -> 16 238 ms and 128 -> 32 372 ms (128 ->
+// 16 607 ms, 128 -> 64 312 ms).  So: a band of width <= 16 the b -> 1
+// kernel supports goes straight to 1; a band of 128 or more first goes to
+// 32; a wider band that 16 divides goes to 16; otherwise to the widest
+// supported width that divides it, or is halved; an odd band finishes with
+// b -> 1.  b0 = 128 gives 128 -> 32 -> 16 -> 1, b0 = 64 gives 64 -> 16 -> 1.
 static int schedule(int b0, int elem, int *out) {
     int k = 0;
     out[k++] = b0;
     while (out[k - 1] > 1) {
         const int b = out[k - 1];
         int next = b % 2 != 0 ? 1 : b / 2;
-        if (band_tri_supported(b, elem)) {
+        if (b <= 16 && band_tri_supported(b, elem)) {
+            next = 1;
+        } else if (b >= 128 && b % 32 == 0) {
+            next = 32;
+        } else if (b > 16 && b % 16 == 0) {
+            next = 16;
+        } else if (band_tri_supported(b, elem)) {
             next = 1;
         } else {
-            for (int w = 32; w >= 2; w >>= 1)
+            for (int w = 16; w >= 2; w >>= 1)
                 if (band_tri_supported(w, elem) && b % w == 0 && w < b) {
                     next = w;
                     break;

@@ -68,6 +68,13 @@ namespace sev {
 // wait is capped and an abort turns the remaining steps into no-ops so that
 // every warp still reaches its barriers.  The ring holds (3G + 3) b + 2
 // columns.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, int src_bytes) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int B, int G>
 __host__ __device__ constexpr int tri_wcap() {
     return (3 * G + 3) * B + 2;
@@ -79,7 +86,8 @@ __device__ __forceinline__ void named_bar(int id, int nthreads) {
 
 template <typename T, int B, int G>
 __global__ void __launch_bounds__((G + 2) * 32, 1)
-    band_tri_kernel(int n, T *AB, int ldab, int nsweeps, int ngroups, int *progress, int *group_ctr, int *err) {
+    band_tri_kernel(int n, T *AB, int ldab, int nsweeps, int ngroups, int *progress, int *group_ctr, int *err,
+                    int async_ok) {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int LDW = 2 * B;
     constexpr int wcap = tri_wcap<B, G>();
@@ -171,6 +179,17 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
             // ------------------------------------------------------- loader
             int loaded_hi = i0 - 1, seen = 0;
             for (int ts = 1; ts <= Jf && !s_abort; ++ts) {
+                if (async_ok && ts > 1) {
+                    // the previous step's copies land and are published before
+                    // this step waits for anything (the ring-space wait depends
+                    // on compute having consumed them)
+                    cp_async_wait_all();
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        s_avail = ts - 1;
+                    }
+                }
                 if (gi > 0 && ts + 2 > seen) {
                     const int need = (ts + 2 <= Jprev) ? ts + 2 : kTriInf;
                     int pv = 0;
@@ -211,8 +230,23 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                 }
                 __syncwarp();
                 if (s_abort) break;
-                {
-                    const int c0 = loaded_hi;
+                const int c0 = loaded_hi;
+                if (async_ok) {
+                    // asynchronous 16-byte copies (zero-filled past the matrix
+                    // end), all issued at once: a step costs one memory latency
+                    // instead of one per batch of loads; published at the top of
+                    // the next iteration (or after the loop)
+                    constexpr int EPC = 16 / (int)sizeof(T);  // elements per chunk
+                    constexpr int CH = LDW / EPC;             // chunks per column
+                    for (int q = lane; q < (hi - c0) * CH; q += 32) {
+                        const int c = c0 + q / CH, d0 = (q % CH) * EPC;
+                        int valid = n - c - d0;
+                        valid = valid < 0 ? 0 : (valid > EPC ? EPC : valid);
+                        const T *src = valid > 0 ? AB + d0 + (size_t)c * ldab : AB;
+                        cp_async16(W.w + (size_t)(c % wcap) * LDW + d0, src, valid * (int)sizeof(T));
+                    }
+                    cp_async_commit();
+                } else {
                     batched_copy<T, 16>(
                         (hi - c0) * LDW, lane, 32,
                         [&](int k) {
@@ -220,13 +254,22 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                             return (c + d < n) ? __ldcg(AB + d + (size_t)c * ldab) : T(0);
                         },
                         [&](int k, T v) { W.w[((c0 + k / LDW) % wcap) * LDW + k % LDW] = v; });
+                    __syncwarp();
+                    if (lane == 0) {
+                        __threadfence_block();
+                        s_avail = ts;
+                    }
                 }
                 loaded_hi = max(loaded_hi, hi);
+                if (lane == 0) TRACE(gi, ts, 7, clock64());
+            }
+            if (async_ok) {
+                // every copy in flight lands before the loader publishes or leaves
+                cp_async_wait_all();
                 __syncwarp();
-                if (lane == 0) {
+                if (lane == 0 && !s_abort) {
                     __threadfence_block();
-                    s_avail = ts;
-                    TRACE(gi, ts, 7, clock64());
+                    s_avail = Jf;
                 }
             }
         } else if (writer) {
@@ -290,10 +333,24 @@ static int launch_tri(sev_ctx *h, int n, T *AB, int ldab, int *progress, int *ct
     const int busy = J1 / (3 * G) + 16;
     if (grid > busy) grid = busy;
     if (grid > ngroups) grid = ngroups;
+    // 16-byte asynchronous copies need a 16-byte-aligned band and column stride
+    const int async_ok = ((uintptr_t)AB % 16 == 0) && ((size_t)ldab * sizeof(T)) % 16 == 0;
     SEV_LAUNCH(h, K_BAND_TRI, kern, grid, (G + 2) * 32, smem, n, AB, ldab, nsweeps, ngroups, progress, ctr,
-               h->d_err);
+               h->d_err, async_ok);
     return SEV_OK;
 }
+
+// Compute warps (sweeps) per CTA: fewer per CTA spreads the concurrently
+// active sweeps over more SMs.
+#ifndef SEV_TRI_G_SMALL
+#define SEV_TRI_G_SMALL 8
+#endif
+#ifndef SEV_TRI_G16
+#define SEV_TRI_G16 4
+#endif
+#ifndef SEV_TRI_G32
+#define SEV_TRI_G32 4
+#endif
 
 int band_tri_supported(int b, int elem) { return b == 2 || b == 4 || b == 8 || b == 16 || (b == 32 && elem == 4); }
 
@@ -313,14 +370,12 @@ int launch_band_tri(sev_ctx *h, int n, T *AB, int ldab, int b, void *ws, size_t 
     int *progress = c.take<int>((size_t)n + 1);
     int *ctr = c.take<int>(1);
     switch (b) {
-        case 2: return launch_tri<T, 2, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
-        case 4: return launch_tri<T, 4, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
-        case 8: return launch_tri<T, 8, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
-        case 16:
-            if constexpr (sizeof(T) == 8) return launch_tri<T, 16, 7>(h, n, AB, ldab, progress, ctr, nsweeps);
-            return launch_tri<T, 16, 8>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 2: return launch_tri<T, 2, SEV_TRI_G_SMALL>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 4: return launch_tri<T, 4, SEV_TRI_G_SMALL>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 8: return launch_tri<T, 8, SEV_TRI_G_SMALL>(h, n, AB, ldab, progress, ctr, nsweeps);
+        case 16: return launch_tri<T, 16, SEV_TRI_G16>(h, n, AB, ldab, progress, ctr, nsweeps);
         case 32:
-            if constexpr (sizeof(T) == 4) return launch_tri<T, 32, 7>(h, n, AB, ldab, progress, ctr, nsweeps);
+            if constexpr (sizeof(T) == 4) return launch_tri<T, 32, SEV_TRI_G32>(h, n, AB, ldab, progress, ctr, nsweeps);
             return SEV_ERR_UNSUPPORTED;
         default: return SEV_ERR_UNSUPPORTED;
     }

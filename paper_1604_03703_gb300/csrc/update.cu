@@ -127,6 +127,174 @@ __global__ void __launch_bounds__(256) symm_kernel(int N, int b, const T *__rest
         }
 }
 
+// Y = A22 U for FP32 data: 128 x 64 output tiles, 8 x 4 outputs per thread,
+// K in steps of 16 through double-buffered shared memory (the next step's
+// loads in registers while this one is multiplied), float4 loads of A22 in
+// whichever orientation is contiguous (columns below the diagonal block,
+// rows -- A(m, k) = A(k, m) -- above it, transposed into shared memory),
+// and the K range split over blockIdx.z with per-split partial tiles
+// (summed in a fixed order by symm_reduce_kernel) so that every SM has work.
+// Needs lda % 4 == 0 and a 16-byte-aligned A22.
+constexpr int SBM = 128, SBN = 64, SBK = 16;
+
+struct SymmSmem {
+    float As[2][SBK][SBM + 4];
+    float Bs[2][SBK][SBN + 4];
+};
+
+__device__ __forceinline__ void symm_load_a(float4 (&ra)[2], float (&rs)[8], bool &vec, int &mode, const float *A,
+                                            int lda, int N, int m0, int k0) {
+    const int tid = threadIdx.x;
+    const bool inside = m0 + SBM <= N && k0 + SBK <= N;
+    if (inside && k0 + SBK <= m0) {  // strictly below: columns are contiguous
+        mode = 0;
+        vec = true;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + r * 256, k = idx >> 5, mq = idx & 31;
+            ra[r] = *reinterpret_cast<const float4 *>(A + (size_t)(m0 + 4 * mq) + (size_t)(k0 + k) * lda);
+        }
+    } else if (inside && k0 >= m0 + SBM) {  // strictly above: A(m, k) = A(k, m), rows contiguous
+        mode = 1;
+        vec = true;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + r * 256, m = idx >> 2, kq = idx & 3;
+            ra[r] = *reinterpret_cast<const float4 *>(A + (size_t)(k0 + 4 * kq) + (size_t)(m0 + m) * lda);
+        }
+    } else {  // crosses the diagonal block or the matrix edge: element by element
+        mode = 2;
+        vec = false;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int idx = tid + r * 256, m = idx & (SBM - 1), k = idx >> 7;
+            const int gm = m0 + m, gk = k0 + k;
+            float v = 0.f;
+            if (gm < N && gk < N) v = gm >= gk ? A[(size_t)gm + (size_t)gk * lda] : A[(size_t)gk + (size_t)gm * lda];
+            rs[r] = v;
+        }
+    }
+}
+
+__device__ __forceinline__ void symm_store_a(SymmSmem &S, int buf, const float4 (&ra)[2], const float (&rs)[8],
+                                             int mode) {
+    const int tid = threadIdx.x;
+    if (mode == 0) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + r * 256, k = idx >> 5, mq = idx & 31;
+            *reinterpret_cast<float4 *>(&S.As[buf][k][4 * mq]) = ra[r];
+        }
+    } else if (mode == 1) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int idx = tid + r * 256, m = idx >> 2, kq = idx & 3;
+            S.As[buf][4 * kq + 0][m] = ra[r].x;
+            S.As[buf][4 * kq + 1][m] = ra[r].y;
+            S.As[buf][4 * kq + 2][m] = ra[r].z;
+            S.As[buf][4 * kq + 3][m] = ra[r].w;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int idx = tid + r * 256, m = idx & (SBM - 1), k = idx >> 7;
+            S.As[buf][k][m] = rs[r];
+        }
+    }
+}
+
+__device__ __forceinline__ void symm_load_b(float (&rb)[4], const float *U, int ldu, int N, int b, int k0, int n0) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int idx = threadIdx.x + r * 256, k = idx & (SBK - 1), n = idx >> 4;
+        const int gk = k0 + k, gn = n0 + n;
+        rb[r] = (gk < N && gn < b) ? U[(size_t)gk + (size_t)gn * ldu] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void symm_store_b(SymmSmem &S, int buf, const float (&rb)[4]) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int idx = threadIdx.x + r * 256, k = idx & (SBK - 1), n = idx >> 4;
+        S.Bs[buf][k][n] = rb[r];
+    }
+}
+
+__global__ void __launch_bounds__(256) symm_f32_kernel(int N, int b, const float *__restrict__ A, int lda,
+                                                       const float *__restrict__ U, int ldu, int kchunk,
+                                                       float *__restrict__ Yout, int ldy, size_t split_stride) {
+    __shared__ __align__(16) SymmSmem S;
+    const int m0 = blockIdx.x * SBM, n0 = blockIdx.y * SBN;
+    const int kbeg = blockIdx.z * kchunk, kend = min(N, kbeg + kchunk);
+    float *Y = Yout + (size_t)blockIdx.z * split_stride;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    float4 ra[2];
+    float rs[8], rb[4];
+    bool vec;
+    int mode;
+    int buf = 0;
+    if (kbeg < kend) {
+        symm_load_a(ra, rs, vec, mode, A, lda, N, m0, kbeg);
+        symm_load_b(rb, U, ldu, N, b, kbeg, n0);
+        symm_store_a(S, 0, ra, rs, mode);
+        symm_store_b(S, 0, rb);
+    }
+    __syncthreads();
+    for (int k0 = kbeg; k0 < kend; k0 += SBK) {
+        const bool more = k0 + SBK < kend;
+        if (more) {
+            symm_load_a(ra, rs, vec, mode, A, lda, N, m0, k0 + SBK);
+            symm_load_b(rb, U, ldu, N, b, k0 + SBK, n0);
+        }
+        // rows beyond kend in this step are zero-padded only at the matrix
+        // edge; split boundaries are multiples of SBK
+#pragma unroll
+        for (int k = 0; k < SBK; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&S.As[buf][k][4 * tx]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&S.As[buf][k][64 + 4 * tx]);
+            const float4 bv = *reinterpret_cast<const float4 *>(&S.Bs[buf][k][4 * ty]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bw[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bw[j], acc[i][j]);
+        }
+        if (more) {
+            symm_store_a(S, buf ^ 1, ra, rs, mode);
+            symm_store_b(S, buf ^ 1, rb);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int m = m0 + (i < 4 ? 4 * tx + i : 64 + 4 * tx + i - 4);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + 4 * ty + j;
+            if (m < N && n < b) Y[(size_t)m + (size_t)n * ldy] = acc[i][j];
+        }
+    }
+}
+
+// Y = sum over the splits of the partial tiles, in split order.
+__global__ void symm_reduce_kernel(int N, int b, int splits, const float *__restrict__ part, size_t split_stride,
+                                   float *__restrict__ Y, int ldy) {
+    const size_t total = (size_t)N * b;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int m = (int)(idx % N), n = (int)(idx / N);
+        float s = 0.f;
+        for (int z = 0; z < splits; ++z) s += part[(size_t)z * split_stride + idx];
+        Y[(size_t)m + (size_t)n * ldy] = s;
+    }
+}
+
 // C = alpha * A B + beta * D, A (M x K, m contiguous), B (K x Nc, k contiguous, ld ldb).
 // Used for X = Y T and V = 1/2 U Zm - X.
 template <typename T>
@@ -261,9 +429,11 @@ __global__ void __launch_bounds__(256) syr2k_kernel(int N, int b, T *__restrict_
 // --------------------------------------------------------------- driver
 template <typename T>
 struct F2BBuffers {
-    T *U, *Y, *X, *V, *Tm, *Zm, *part;
+    T *U, *Y, *X, *V, *Tm, *Zm, *part, *ypart;
     void *panel_ws, *tc_ws;
 };
+
+constexpr int kSymmMaxSplits = 8;
 
 static int utx_parts(int N) {
     int p = (N + 1023) / 1024;
@@ -279,6 +449,7 @@ static void carve_f2b(Carver &c, F2BBuffers<T> &B, sev_ctx *h, int n, int b, boo
     B.Tm = c.take<T>((size_t)b * b);
     B.Zm = c.take<T>((size_t)b * b);
     B.part = c.take<T>((size_t)utx_parts(n) * b * b);
+    B.ypart = c.take<T>((size_t)kSymmMaxSplits * n * b);
     B.tc_ws = tc ? (void *)c.take<char>(tc_workspace<T>(n, b)) : nullptr;
     B.panel_ws = c.take<char>(panel_workspace<T>(h, n, b));
 }
@@ -313,6 +484,21 @@ int launch_full_to_band(sev_ctx *h, int n, T *A, int lda, int b, T *AB, int ldab
         if (tc_symm_ok) {
             rc = tc_symm<T>(h, N, b, A22, lda, B.U, B.Y, B.tc_ws);
             if (rc) return rc;
+        } else if (sizeof(T) == 4 && lda % 4 == 0 && ((uintptr_t)A22 & 15) == 0) {
+            // split K until the grid covers ~2 CTAs per SM
+            const int mt = (N + SBM - 1) / SBM, nt = (b + SBN - 1) / SBN;
+            int splits = 1;
+            while (splits < kSymmMaxSplits && mt * nt * splits < 2 * h->sm_count && N / (splits * 2) >= 256) splits *= 2;
+            const int kchunk = ((N + splits - 1) / splits + SBK - 1) / SBK * SBK;
+            float *dst = splits > 1 ? (float *)B.ypart : (float *)B.Y;
+            SEV_LAUNCH(h, K_SYMM, symm_f32_kernel, dim3(mt, nt, splits), 256, 0, N, b, (const float *)A22, lda,
+                       (const float *)B.U, N, kchunk, dst, N, (size_t)N * b);
+            if (splits > 1) {
+                int g = (int)(((size_t)N * b + 255) / 256);
+                if (g > h->sm_count * 8) g = h->sm_count * 8;
+                SEV_LAUNCH(h, K_SYMM, symm_reduce_kernel, g, 256, 0, N, b, splits, (const float *)B.ypart,
+                           (size_t)N * b, (float *)B.Y, N);
+            }
         } else {
             SEV_LAUNCH(h, K_SYMM, symm_kernel<T>, dim3((N + BM - 1) / BM, (b + BN - 1) / BN), 256, 0, N, b, A22, lda,
                        B.U, N, B.Y, N);
