@@ -400,6 +400,68 @@ __device__ __forceinline__ void warp_apply2(int m, int k, const T *v, T tk, T *c
     warp_apply4(m, k, v, tk, c0, c1, (T *)nullptr, (T *)nullptr);
 }
 
+// The owner warp's step of cta_qr for FP32 data with the column segment in
+// registers (rows k + lane + 32t, up to 256 rows): apply H_k to it
+// (do_apply), then form reflector k+1 from its rows k+1.. (do_house) --
+// pair-float sum of squares in two independent accumulators, pair-float
+// scalars -- and store the segment once.  Same results as warp_apply2 +
+// warp_house up to the order of the FP32 dot product's terms.
+__device__ __forceinline__ void warp_apply_house_f32(int m, int k, const float *v, float tk, float *col,
+                                                     float *tau_next, bool do_apply, bool do_house) {
+    const int lane = threadIdx.x & 31;
+    float x[8], vv[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int row = k + lane + 32 * t;
+        const bool in = row < m;
+        x[t] = in ? col[row] : 0.f;
+        vv[t] = in ? (row == k ? 1.f : v[row]) : 0.f;
+    }
+    if (do_apply) {
+        float d0 = 0.f, d1 = 0.f;
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            d0 = fmaf(x[t], vv[t], d0);
+            d1 = fmaf(x[t + 1], vv[t + 1], d1);
+        }
+        const float sc = tk * warp_sum(d0 + d1);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) x[t] = fmaf(-sc, vv[t], x[t]);
+    }
+    if (do_house) {
+        F2 a0{0.f, 0.f}, a1{0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int row = k + lane + 32 * t;
+            if (row >= k + 2 && row < m) {
+                if (t & 1)
+                    f2_add_sq(a1, x[t]);
+                else
+                    f2_add_sq(a0, x[t]);
+            }
+        }
+        const F2 acc = warp_sum_f2(f2_add(a0, a1));
+        const float alpha = __shfl_sync(0xffffffffu, x[0], 1);  // row k + 1
+        float tau = 0.f, beta = 0.f, inv = 0.f;
+        house_scalars_f2(alpha, acc, &tau, &beta, &inv);
+        if (tau != 0.f) {
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int row = k + lane + 32 * t;
+                if (row >= k + 2) x[t] *= inv;
+            }
+        }
+        if (lane == 1) x[0] = beta;
+        if (lane == 0) *tau_next = tau;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+        const int row = k + lane + 32 * t;
+        if (row < m) col[row] = x[t];
+    }
+    __syncwarp();
+}
+
 // Householder QR of the m x nc block P (shared memory, column-major, ld):
 // r = min(nc, m-1) reflectors.  At step k the warp `own` = (k+1) mod nw
 // applies H_k to column k+1 and forms reflector k+1 (lookahead) -- and
@@ -423,8 +485,18 @@ __device__ int cta_qr(int m, int nc, T *P, int ld, T *tau, double * /*unused*/) 
         const T *v = P + (size_t)k * ld;
         const int own = (k + 1) % nw;
         if (warp == own) {
-            if (tk != T(0) && k + 1 < nc) warp_apply2(m, k, v, tk, P + (size_t)(k + 1) * ld, (T *)nullptr);
-            if (k + 1 < r) warp_house(m - k - 1, P + (k + 1) + (size_t)(k + 1) * ld, &tau[k + 1]);
+            if constexpr (sizeof(T) == 4) {
+                if (m - k <= 256 && k + 1 < nc) {
+                    warp_apply_house_f32(m, k, (const float *)v, (float)tk, (float *)(P + (size_t)(k + 1) * ld),
+                                         (float *)&tau[k + 1], tk != T(0), k + 1 < r);
+                } else {
+                    if (tk != T(0) && k + 1 < nc) warp_apply2(m, k, v, tk, P + (size_t)(k + 1) * ld, (T *)nullptr);
+                    if (k + 1 < r) warp_house(m - k - 1, P + (k + 1) + (size_t)(k + 1) * ld, &tau[k + 1]);
+                }
+            } else {
+                if (tk != T(0) && k + 1 < nc) warp_apply2(m, k, v, tk, P + (size_t)(k + 1) * ld, (T *)nullptr);
+                if (k + 1 < r) warp_house(m - k - 1, P + (k + 1) + (size_t)(k + 1) * ld, &tau[k + 1]);
+            }
         } else if (tk != T(0)) {
             // the other nw - 1 warps share columns k+2 .. nc-1
             const int q = nw - 1;
@@ -538,11 +610,37 @@ __device__ void cta_gemm(int M, int N, int K, T alpha, const T *A, int lda, cons
 // written twice per panel instead of twice per reflector.  The reflectors
 // and the result are those of cta_qr up to rounding.  T_j (upper, jb x jb)
 // is left in Tblk at columns [j0, j0 + jb) (an kQrNB x nc array, ld kQrNB).
-// Scratch: Wk (kQrNB x nc), Gb (kQrNB x kQrNB).  Returns r = min(nc, m-1).
+// Scratch: Wk (kQrNB x nc), Gb and Rs (kQrNB x kQrNB).  Returns r = min(nc, m-1).
 constexpr int kQrNB = 32;
 
+// Compact-WY factor T (r x r, r <= 32, upper, ldt) from G = V^T V (ldg) and
+// tau by the forward recurrence T[0:k, k] = -tau_k T[0:k, 0:k] G[0:k, k],
+// T[k, k] = tau_k, run by warp 0 (lane a owns row a).  Ends with a
+// __syncthreads.
 template <typename T>
-__device__ int cta_qr_blocked(int m, int nc, T *P, int ld, T *tau, T *Tblk, T *Wk, T *Gb) {
+__device__ void form_t_from_g(int r, const T *G, int ldg, const T *tau, T *Tm, int ldt) {
+    if ((threadIdx.x >> 5) == 0) {
+        const int a = threadIdx.x & 31;
+        for (int k = 0; k < r; ++k) {
+            T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+            int q = 0;
+            for (; q + 4 <= k; q += 4) {  // T[a, q] = 0 for q < a (rows above are written first)
+                s0 += Tm[a + (size_t)q * ldt] * G[q + (size_t)k * ldg];
+                s1 += Tm[a + (size_t)(q + 1) * ldt] * G[q + 1 + (size_t)k * ldg];
+                s2 += Tm[a + (size_t)(q + 2) * ldt] * G[q + 2 + (size_t)k * ldg];
+                s3 += Tm[a + (size_t)(q + 3) * ldt] * G[q + 3 + (size_t)k * ldg];
+            }
+            for (; q < k; ++q) s0 += Tm[a + (size_t)q * ldt] * G[q + (size_t)k * ldg];
+            const T s = (s0 + s1) + (s2 + s3);
+            if (a < 32) Tm[a + (size_t)k * ldt] = a < k ? -tau[k] * s : (a == k ? tau[k] : T(0));
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+template <typename T>
+__device__ int cta_qr_blocked(int m, int nc, T *P, int ld, T *tau, T *Tblk, T *Wk, T *Gb, T *Rs) {
     const int r = nc < m - 1 ? nc : m - 1;
     const int tid = threadIdx.x, nt = blockDim.x;
     if (r <= 0) {
@@ -554,36 +652,39 @@ __device__ int cta_qr_blocked(int m, int nc, T *P, int ld, T *tau, T *Tblk, T *W
         T *Pj = P + j0 + (size_t)j0 * ld;
         const int mj = m - j0;
         const int rj = cta_qr(mj, jb, Pj, ld, tau + j0, nullptr);  // = jb: j0 + jb <= r <= m - 1
-        T *Tj = Tblk + (size_t)j0 * kQrNB;
-        cta_form_t(mj, rj, Pj, ld, tau + j0, Tj, kQrNB, Gb, kQrNB);
-        const int nct = nc - j0 - jb;
-        if (nct <= 0) continue;
-        T *C = Pj + (size_t)jb * ld;
-        // V explicit in place (unit diagonal, zeros above); R's triangle saved in Gb
+        // V explicit in place (unit diagonal, zeros above); R's triangle saved in Rs
         for (int idx = tid; idx < jb * jb; idx += nt) {
             const int i = idx % jb, c = idx / jb;
             if (i <= c) {
-                Gb[i + (size_t)c * kQrNB] = Pj[i + (size_t)c * ld];
+                Rs[i + (size_t)c * kQrNB] = Pj[i + (size_t)c * ld];
                 Pj[i + (size_t)c * ld] = i == c ? T(1) : T(0);
             }
         }
         __syncthreads();
-        cta_gemm<T, true, false>(jb, nct, mj, T(1), Pj, ld, C, ld, T(0), Wk, kQrNB);  // W = V^T C
+        T *Tj = Tblk + (size_t)j0 * kQrNB;
+        cta_gemm<T, true, false>(rj, rj, mj, T(1), Pj, ld, Pj, ld, T(0), Gb, kQrNB);  // G = V^T V
         __syncthreads();
-        for (int c = tid; c < nct; c += nt) {  // W <- T^T W, bottom row first (in place)
-            T *w = Wk + (size_t)c * kQrNB;
-            for (int i = jb - 1; i >= 0; --i) {
-                T acc = 0;
-                for (int q = 0; q <= i; ++q) acc += Tj[q + (size_t)i * kQrNB] * w[q];
-                w[i] = acc;
+        form_t_from_g(rj, Gb, kQrNB, tau + j0, Tj, kQrNB);
+        const int nct = nc - j0 - jb;
+        if (nct > 0) {
+            T *C = Pj + (size_t)jb * ld;
+            cta_gemm<T, true, false>(jb, nct, mj, T(1), Pj, ld, C, ld, T(0), Wk, kQrNB);  // W = V^T C
+            __syncthreads();
+            for (int c = tid; c < nct; c += nt) {  // W <- T^T W, bottom row first (in place)
+                T *w = Wk + (size_t)c * kQrNB;
+                for (int i = jb - 1; i >= 0; --i) {
+                    T acc = 0;
+                    for (int q = 0; q <= i; ++q) acc += Tj[q + (size_t)i * kQrNB] * w[q];
+                    w[i] = acc;
+                }
             }
+            __syncthreads();
+            cta_gemm<T, false, false>(mj, nct, jb, T(-1), Pj, ld, Wk, kQrNB, T(1), C, ld);  // C -= V W
+            __syncthreads();
         }
-        __syncthreads();
-        cta_gemm<T, false, false>(mj, nct, jb, T(-1), Pj, ld, Wk, kQrNB, T(1), C, ld);  // C -= V W
-        __syncthreads();
         for (int idx = tid; idx < jb * jb; idx += nt) {
             const int i = idx % jb, c = idx / jb;
-            if (i <= c) Pj[i + (size_t)c * ld] = Gb[i + (size_t)c * kQrNB];
+            if (i <= c) Pj[i + (size_t)c * ld] = Rs[i + (size_t)c * kQrNB];
         }
         __syncthreads();
     }

@@ -102,11 +102,12 @@ __global__ void __launch_bounds__(kThreads)
     T *Tblk = tl + b;
     T *Wk = Tblk + (size_t)kQrNB * b;
     T *Gb = Wk + (size_t)kQrNB * b;
+    T *Rs = Gb + kQrNB * kQrNB;
     batched_copy<T>(
         rows * b, threadIdx.x, blockDim.x, [&](int k) { return P[(size_t)(row0 + k % rows) + (size_t)(k / rows) * ldp]; },
         [&](int k, T v) { S[k % rows + (size_t)(k / rows) * ld] = v; });
     __syncthreads();
-    const int r = cta_qr_blocked(rows, b, S, ld, tl, Tblk, Wk, Gb);
+    const int r = cta_qr_blocked(rows, b, S, ld, tl, Tblk, Wk, Gb, Rs);
     for (int idx = threadIdx.x; idx < rows * b; idx += blockDim.x) {
         const int i = idx % rows, c = idx / rows;
         T v = 0;
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(kThreads)
     T *Tblk = tl + b;
     T *Wk = Tblk + (size_t)kQrNB * b;
     T *Gb = Wk + (size_t)kQrNB * b;
+    T *Rs = Gb + kQrNB * kQrNB;
     batched_copy<T>(
         rows * b, threadIdx.x, blockDim.x,
         [&](int k) {
@@ -156,7 +158,7 @@ __global__ void __launch_bounds__(kThreads)
         },
         [&](int k, T v) { S[k % rows + (size_t)(k / rows) * ld] = v; });
     __syncthreads();
-    const int r = cta_qr_blocked(rows, b, S, ld, tl, Tblk, Wk, Gb);
+    const int r = cta_qr_blocked(rows, b, S, ld, tl, Tblk, Wk, Gb, Rs);
     T *Y = Ynode + (size_t)p * ynode_stride;
     for (int idx = threadIdx.x; idx < kQrNB * b; idx += blockDim.x) Tbuf[(size_t)node * kQrNB * b + idx] = Tblk[idx];
     for (int idx = threadIdx.x; idx < rows * b; idx += blockDim.x) {
@@ -415,12 +417,12 @@ __global__ void __launch_bounds__(kThreads)
 template <typename T>
 static size_t smem_leaf_qr(int r_leaf, int b) {
     // block, tau, T blocks, GEMM scratch, R save, reduction scratch
-    return sizeof(T) * ((size_t)((2 * r_leaf) | 1) * b + b + 2 * (size_t)kQrNB * b + kQrNB * kQrNB) + 16 +
+    return sizeof(T) * ((size_t)((2 * r_leaf) | 1) * b + b + 2 * (size_t)kQrNB * b + 2 * kQrNB * kQrNB) + 16 +
            32 * sizeof(double);
 }
 template <typename T>
 static size_t smem_node_qr(int F, int b) {
-    return sizeof(T) * ((size_t)((F * b) | 1) * b + b + 2 * (size_t)kQrNB * b + kQrNB * kQrNB) + 16 +
+    return sizeof(T) * ((size_t)((F * b) | 1) * b + b + 2 * (size_t)kQrNB * b + 2 * kQrNB * kQrNB) + 16 +
            32 * sizeof(double);
 }
 template <typename T>
