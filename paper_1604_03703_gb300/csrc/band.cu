@@ -159,9 +159,16 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         __syncthreads();
         return;
     }
-    // 3. U, T and U T
+    // 3. U, T and U T (T from G = U^T U by one warp's recurrence when h <= 32)
     cta_extract_u(n_r, nr, nr, S.Xs, ldb1, S.Us, ldb1);
-    cta_form_t(n_r, nr, S.Xs, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
+    if (nr <= 32) {
+        __syncthreads();
+        cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Us, ldb1, T(0), S.Zs, ldh1);
+        __syncthreads();
+        form_t_from_g(nr, S.Zs, ldh1, S.tau, S.Ts, ldh1);
+    } else {
+        cta_form_t(n_r, nr, S.Xs, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
+    }
     cta_gemm<T, false, false>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, T(0), S.UTs, ldb1);
     __syncthreads();
     BTRACE(3);
@@ -188,15 +195,15 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     // V_d = -W_d + 1/2 U Z  (into Ws)
     cta_gemm<T, false, false>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, T(-1), S.Ws, ldb1);
     __syncthreads();
-    // X_d += U V_d^T + V_d U^T (lower half stored)
+    // X_d += U V_d^T + V_d U^T (register-tiled products in shared memory; lower half stored)
+    cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, T(1), S.Xs, ldb1);
+    __syncthreads();
+    cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
+    __syncthreads();
     for (int idx = tid; idx < n_r * n_r; idx += nt) {
         const int r = idx % n_r, c = idx / n_r;
         if (r < c) continue;
-        T s = 0;
-        for (int m = 0; m < nr; ++m)
-            s += S.Us[r + (size_t)m * ldb1] * S.Ws[c + (size_t)m * ldb1] +
-                 S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
-        bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
+        bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
     }
     __syncthreads();
     BTRACE(4);
@@ -214,11 +221,11 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
             __syncthreads();
             cta_gemm<T, false, false>(rows, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
             __syncthreads();
+            cta_gemm<T, false, true>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
+            __syncthreads();
             for (int idx = tid; idx < rows * n_r; idx += nt) {
                 const int r = idx % rows, c = idx / rows;
-                T s = 0;
-                for (int m = 0; m < nr; ++m) s += S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
-                bst_sym(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] - s, bad);
+                bst_sym(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
             }
             __syncthreads();
         }

@@ -624,7 +624,7 @@ __device__ void form_t_from_g(int r, const T *G, int ldg, const T *tau, T *Tm, i
         for (int k = 0; k < r; ++k) {
             T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
             int q = 0;
-            for (; q + 4 <= k; q += 4) {  // T[a, q] = 0 for q < a (rows above are written first)
+            for (; q + 4 <= k; q += 4) {  // T[a, q] = 0 for q < a (written at step q); rows a >= r unused
                 s0 += Tm[a + (size_t)q * ldt] * G[q + (size_t)k * ldg];
                 s1 += Tm[a + (size_t)(q + 1) * ldt] * G[q + 1 + (size_t)k * ldg];
                 s2 += Tm[a + (size_t)(q + 2) * ldt] * G[q + 2 + (size_t)k * ldg];
@@ -632,7 +632,7 @@ __device__ void form_t_from_g(int r, const T *G, int ldg, const T *tau, T *Tm, i
             }
             for (; q < k; ++q) s0 += Tm[a + (size_t)q * ldt] * G[q + (size_t)k * ldg];
             const T s = (s0 + s1) + (s2 + s3);
-            if (a < 32) Tm[a + (size_t)k * ldt] = a < k ? -tau[k] * s : (a == k ? tau[k] : T(0));
+            if (a < r) Tm[a + (size_t)k * ldt] = a < k ? -tau[k] * s : (a == k ? tau[k] : T(0));
             __syncwarp();
         }
     }
