@@ -69,10 +69,6 @@ __device__ __forceinline__ T bld(const T *AB, int ldab, int n, int r, int c, int
     return __ldcg(AB + d + (size_t)c * ldab);
 }
 template <typename T>
-__device__ __forceinline__ T bld_sym(const T *AB, int ldab, int n, int u, int q, int *bad) {
-    return u >= q ? bld(AB, ldab, n, u, q, bad) : bld(AB, ldab, n, q, u, bad);
-}
-template <typename T>
 __device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, int *bad) {
     const int d = r - c;
     if (d < 0 || d >= ldab || r >= n || c < 0) {
@@ -81,14 +77,6 @@ __device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, i
     }
     AB[d + (size_t)c * ldab] = v;
 }
-template <typename T>
-__device__ __forceinline__ void bst_sym(T *AB, int ldab, int n, int u, int q, T v, int *bad) {
-    if (u >= q)
-        bst(AB, ldab, n, u, q, v, bad);
-    else
-        bst(AB, ldab, n, q, u, v, bad);
-}
-
 template <typename T>
 struct ChaseSmem {
     T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau;
@@ -173,16 +161,32 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     __syncthreads();
     BTRACE(3);
     // 4. the qr-row diagonal block X_d (n_r x n_r): two-sided update
+    // (the stored lower triangle, read down its columns, then mirrored in shared memory)
     batched_copy<T>(
-        n_r * n_r, tid, nt, [&](int k) { return bld_sym(AB, ldab, n, o_qr_r + k % n_r, o_qr_r + k / n_r, bad); },
-        [&](int k, T v) { S.Xs[k % n_r + (size_t)(k / n_r) * ldb1] = v; });
+        n_r * n_r, tid, nt,
+        [&](int k) {
+            const int r = k % n_r, c = k / n_r;
+            return r >= c ? bld(AB, ldab, n, o_qr_r + r, o_qr_r + c, bad) : T(0);
+        },
+        [&](int k, T v) {
+            const int r = k % n_r, c = k / n_r;
+            if (r >= c) S.Xs[r + (size_t)c * ldb1] = v;
+        });
     __syncthreads();
+    for (int idx = tid; idx < n_r * n_r; idx += nt) {
+        const int r = idx % n_r, c = idx / n_r;
+        if (r < c) S.Xs[r + (size_t)c * ldb1] = S.Xs[c + (size_t)r * ldb1];
+    }
+    __syncthreads();
+    BTRACE(6);
     // W_d = X_d (U T)
     cta_gemm<T, false, false>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
     __syncthreads();
+    BTRACE(7);
     // S = U^T W_d
     cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Ws, ldb1, T(0), S.Zs, ldh1);
     __syncthreads();
+    BTRACE(8);
     // Z = T^T S, in place column by column (rows descending)
     for (int c = tid; c < nr; c += nt) {
         for (int a = nr - 1; a >= 0; --a) {
@@ -195,11 +199,13 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     // V_d = -W_d + 1/2 U Z  (into Ws)
     cta_gemm<T, false, false>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, T(-1), S.Ws, ldb1);
     __syncthreads();
+    BTRACE(9);
     // X_d += U V_d^T + V_d U^T (register-tiled products in shared memory; lower half stored)
     cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, T(1), S.Xs, ldb1);
     __syncthreads();
     cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
     __syncthreads();
+    BTRACE(10);
     for (int idx = tid; idx < n_r * n_r; idx += nt) {
         const int r = idx % n_r, c = idx / n_r;
         if (r < c) continue;
@@ -214,18 +220,37 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         const int a_end = part == 0 ? o_v : n_c;
         for (int a0 = a_begin; a0 < a_end; a0 += b) {
             const int rows = min(b, a_end - a0);
-            batched_copy<T>(
-                rows * n_r, tid, nt,
-                [&](int k) { return bld_sym(AB, ldab, n, o_up_c + a0 + k % rows, o_qr_r + k / rows, bad); },
-                [&](int k, T v) { S.Xs[k % rows + (size_t)(k / rows) * ldb1] = v; });
+            if (part == 0) {
+                // rows above the qr rows: element (row, col) is stored as (col, row), contiguous
+                // along col -- consecutive threads take consecutive columns
+                batched_copy<T>(
+                    rows * n_r, tid, nt,
+                    [&](int k) { return bld(AB, ldab, n, o_qr_r + k % n_r, o_up_c + a0 + k / n_r, bad); },
+                    [&](int k, T v) { S.Xs[k / n_r + (size_t)(k % n_r) * ldb1] = v; });
+            } else {
+                batched_copy<T>(
+                    rows * n_r, tid, nt,
+                    [&](int k) { return bld(AB, ldab, n, o_up_c + a0 + k % rows, o_qr_r + k / rows, bad); },
+                    [&](int k, T v) { S.Xs[k % rows + (size_t)(k / rows) * ldb1] = v; });
+            }
             __syncthreads();
+            if (part == 1 && a0 == a_begin) BTRACE(11);
             cta_gemm<T, false, false>(rows, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
             __syncthreads();
+            if (part == 1 && a0 == a_begin) BTRACE(12);
             cta_gemm<T, false, true>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
             __syncthreads();
-            for (int idx = tid; idx < rows * n_r; idx += nt) {
-                const int r = idx % rows, c = idx / rows;
-                bst_sym(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
+            if (part == 1 && a0 == a_begin) BTRACE(13);
+            if (part == 0) {
+                for (int idx = tid; idx < rows * n_r; idx += nt) {
+                    const int c = idx % n_r, r = idx / n_r;
+                    bst(AB, ldab, n, o_qr_r + c, o_up_c + a0 + r, S.Xs[r + (size_t)c * ldb1], bad);
+                }
+            } else {
+                for (int idx = tid; idx < rows * n_r; idx += nt) {
+                    const int r = idx % rows, c = idx / rows;
+                    bst(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
+                }
             }
             __syncthreads();
         }
@@ -307,6 +332,11 @@ int launch_band_to_band(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, void 
     SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_chase_kernel<T>, kThreads, smem));
     if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
     int grid = hd->sm_count * per_sm;
+    // sweep i runs ~3 chases behind sweep i - 1, so about J/3 sweeps (J the
+    // chases of the first) progress at once; CTAs beyond that would only poll
+    // the progress flags of their predecessors and load the L2 with it
+    const int busy = band_num_chases(n, b, h, 0) / 3 + 8;
+    if (grid > busy) grid = busy;
     if (grid > nsweeps) grid = nsweeps;
     SEV_LAUNCH(hd, K_BAND_CHASE, band_chase_kernel<T>, grid, kThreads, smem, n, AB, ldab, b, h, nsweeps, progress,
                ctr, hd->d_err);
