@@ -200,6 +200,17 @@ def kernel_model(name, n, b0, elem):
     return None, None, None
 
 
+# DRAM bytes (dram__bytes_read + dram__bytes_write) per step of the bench's
+# dominant kernel, from the ncu capture summarised under profiles/.
+MEASURED_TRAFFIC = {
+    "band_chase": {
+        "bytes_per_step": 2 * 4 * 4.55e6,
+        "note": "profiles/band_chase_n4096_b128to32.md: 4.55 MB per 128->32 launch at n=4096, scaled by n "
+                "(the band is L2-resident and moves through DRAM about once) to n=16384, two launches per step",
+    },
+}
+
+
 def roofline(name, amount, unit, bound, ms_per_step, peaks, clocks, elem):
     if amount is None or ms_per_step <= 0:
         return None
@@ -558,7 +569,10 @@ def run_ours(args):
     roof = roofline(dominant, amount, unit, bound, dom_ms_step, peaks, clk, 4)
     if roof is not None:
         roof["kernel"] = dominant
-        roof["traffic"] = None
+        traffic = MEASURED_TRAFFIC.get(dominant) if (n, b0) == (16384, 128) else None
+        roof["traffic"] = traffic["bytes_per_step"] if traffic else None
+        if traffic:
+            roof["traffic_note"] = traffic["note"]
         roof["launches_per_step"] = prof[dominant][1]
         roof["ms_per_step"] = dom_ms_step
 

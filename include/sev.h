@@ -204,7 +204,7 @@ int sev_eigvalsh_batched(sev_handle handle, int count, const int *n, const int *
                          double *const *eigs);
 /*
  * Autotuner of the batched band width: times the batched launch on
- * synthetic matrices with a strided sample (at most 512) of the sizes n[]
+ * synthetic matrices with a strided sample (at most 4096) of the sizes n[]
  * for every supported b, stores the fastest in the handle (used when a plan
  * passes b = 0) and returns it in *b_best (0 if no size fits the batched
  * kernel).  Allocates and synchronises.

@@ -587,13 +587,13 @@ int sev_batch_autotune(sev_handle h, int count, const int *n, int prec, int *b_b
     if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
     const int elem = prec == SEV_FP64 ? 8 : 4;
     const int cands[] = {4, 8, 16, 32};
-    // a strided sample (at most 512) of the sizes that fit the batched kernel at the narrowest band
+    // a strided sample (at most 4096) of the sizes that fit the batched kernel at the narrowest band
     std::vector<int> sizes;
     for (int i = 0; i < count; ++i)
         if (n[i] > 0 && batch_fits(h, prec, 8, n[i])) sizes.push_back(n[i]);
     std::sort(sizes.begin(), sizes.end());
     std::vector<int> sample;
-    const size_t want = sizes.size() < 512 ? sizes.size() : 512;
+    const size_t want = sizes.size() < 4096 ? sizes.size() : 4096;
     for (size_t k = 0; k < want; ++k) sample.push_back(sizes[k * sizes.size() / want]);
     *b_best = 0;
     if (sample.empty()) return SEV_OK;
