@@ -200,16 +200,29 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     cta_gemm<T, false, false>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, T(-1), S.Ws, ldb1);
     __syncthreads();
     BTRACE(9);
-    // X_d += U V_d^T + V_d U^T (register-tiled products in shared memory; lower half stored)
-    cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, T(1), S.Xs, ldb1);
-    __syncthreads();
-    cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
-    __syncthreads();
-    BTRACE(10);
-    for (int idx = tid; idx < n_r * n_r; idx += nt) {
-        const int r = idx % n_r, c = idx / n_r;
-        if (r < c) continue;
-        bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
+    // X_d += U V_d^T + V_d U^T, lower half stored: register-tiled products for
+    // wide blocks, one element per thread for narrow ones (more threads busy)
+    if (n_r >= 64) {
+        cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, T(1), S.Xs, ldb1);
+        __syncthreads();
+        cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
+        __syncthreads();
+        BTRACE(10);
+        for (int idx = tid; idx < n_r * n_r; idx += nt) {
+            const int r = idx % n_r, c = idx / n_r;
+            if (r < c) continue;
+            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
+        }
+    } else {
+        for (int idx = tid; idx < n_r * n_r; idx += nt) {
+            const int r = idx % n_r, c = idx / n_r;
+            if (r < c) continue;
+            T s = 0;
+            for (int m = 0; m < nr; ++m)
+                s += S.Us[r + (size_t)m * ldb1] * S.Ws[c + (size_t)m * ldb1] +
+                     S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
+            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
+        }
     }
     __syncthreads();
     BTRACE(4);
@@ -238,18 +251,28 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
             cta_gemm<T, false, false>(rows, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
             __syncthreads();
             if (part == 1 && a0 == a_begin) BTRACE(12);
-            cta_gemm<T, false, true>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
-            __syncthreads();
+            // X <- X - W U^T: register-tiled for wide blocks, else folded into the stores
+            const bool tiled = n_r >= 64;
+            if (tiled) {
+                cta_gemm<T, false, true>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
+                __syncthreads();
+            }
             if (part == 1 && a0 == a_begin) BTRACE(13);
+            auto updated = [&](int r, int c) {
+                T v = S.Xs[r + (size_t)c * ldb1];
+                if (!tiled)
+                    for (int m = 0; m < nr; ++m) v -= S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
+                return v;
+            };
             if (part == 0) {
                 for (int idx = tid; idx < rows * n_r; idx += nt) {
                     const int c = idx % n_r, r = idx / n_r;
-                    bst(AB, ldab, n, o_qr_r + c, o_up_c + a0 + r, S.Xs[r + (size_t)c * ldb1], bad);
+                    bst(AB, ldab, n, o_qr_r + c, o_up_c + a0 + r, updated(r, c), bad);
                 }
             } else {
                 for (int idx = tid; idx < rows * n_r; idx += nt) {
                     const int r = idx % rows, c = idx / rows;
-                    bst(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
+                    bst(AB, ldab, n, o_up_c + a0 + r, o_qr_r + c, updated(r, c), bad);
                 }
             }
             __syncthreads();

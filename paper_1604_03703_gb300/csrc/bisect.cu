@@ -455,10 +455,11 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     int per_sm = 0;
     SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bisect_rounds_kernel, kBisThreads, 0));
     if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
-    // A Sturm step has one FMA on its dependence chain and three FP64
-    // instructions in all; about 64 chains per SM keep the FP64 pipe busy
-    // through that latency.  Rounds are sized to that budget; 1024 threads
-    // per CTA run a round of up to 150K chains in a single pass.
+    // A Sturm step is three FP64 instructions on its dependence chain.  The
+    // budget of chains per round (64 per SM) is the measured best at
+    // n = 16384 (256 per SM, which makes late rounds take two levels of
+    // three chains each, ran 18 % slower); 1024 threads per CTA run a round
+    // of up to 150K chains in a single pass.
     const int grid = h->sm_count;
     int budget = grid * 64;
     int maxit = 200;

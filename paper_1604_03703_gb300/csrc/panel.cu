@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(kThreads)
     const int ld = b + 1;
     T *M = (T *)smem;                 // LU in place: U1 strictly lower, W1 upper
     T *Inv = M + (size_t)ld * b;      // W1^{-1}, then U1^{-1}
-    T *Sg = Inv + (size_t)ld * b;     // signs
+    T *WS = Inv + (size_t)ld * b;     // W1 S
+    T *Sg = WS + (size_t)ld * b;      // signs
     batched_copy<T>(
         b * b, threadIdx.x, blockDim.x, [&](int k) { return Q[k % b + (size_t)(k / b) * ldq]; },
         [&](int k, T v) { M[k % b + (size_t)(k / b) * ld] = v; });
@@ -299,24 +300,31 @@ __global__ void __launch_bounds__(kThreads)
         }
         __syncthreads();
     }
-    // W1^{-1} (upper): column c solves W1 x = e_c by back substitution
-    for (int c = threadIdx.x; c < b; c += blockDim.x) {
-        for (int i = b - 1; i >= 0; --i) {
-            if (i > c) {
-                Inv[i + (size_t)c * ld] = 0;
-                continue;
-            }
-            T s = (i == c) ? T(1) : T(0);
-            for (int q = i + 1; q <= c; ++q) s -= M[i + (size_t)q * ld] * Inv[q + (size_t)c * ld];
-            Inv[i + (size_t)c * ld] = s / M[i + (size_t)i * ld];
-        }
+    // W1^{-1} (upper) by column-sweep back substitution, all columns at once:
+    // Inv = I; for q = b-1 .. 0: row q /= W1[q,q], then rows i < q lose
+    // W1[i,q] times row q (columns c >= q).
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+        const int i = idx % b, c = idx / b;
+        Inv[i + (size_t)c * ld] = i == c ? T(1) : T(0);
     }
     __syncthreads();
+    for (int q = b - 1; q >= 0; --q) {
+        const T piv = M[q + (size_t)q * ld];
+        for (int c = q + threadIdx.x; c < b; c += blockDim.x) Inv[q + (size_t)c * ld] /= piv;
+        __syncthreads();
+        const int w = b - q;
+        for (int idx = threadIdx.x; idx < q * w; idx += blockDim.x) {
+            const int i = idx % q, c = q + idx / q;
+            Inv[i + (size_t)c * ld] -= M[i + (size_t)q * ld] * Inv[q + (size_t)c * ld];
+        }
+        __syncthreads();
+    }
     for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) Winv[idx] = Inv[idx % b + (size_t)(idx / b) * ld];
-    // U[0:b, :] = U1 (unit lower)
+    // U[0:b, :] = U1 (unit lower); W1 S (upper, zeros below) into WS
     for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
         const int i = idx % b, c = idx / b;
         U[i + (size_t)c * ldu] = i < c ? T(0) : (i == c ? T(1) : M[i + (size_t)c * ld]);
+        WS[i + (size_t)c * ld] = i <= c ? M[i + (size_t)c * ld] * Sg[c] : T(0);
     }
     // band block S R (rows scaled by S), zeros below the diagonal
     for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
@@ -324,26 +332,23 @@ __global__ void __launch_bounds__(kThreads)
         Apanel[i + (size_t)c * lda] = i <= c ? Sg[i] * Rroot[idx] : T(0);
     }
     __syncthreads();
-    // U1^{-1} (unit lower): column c by forward substitution
-    for (int c = threadIdx.x; c < b; c += blockDim.x) {
-        for (int i = 0; i < b; ++i) {
-            if (i < c) {
-                Inv[i + (size_t)c * ld] = 0;
-                continue;
-            }
-            T s = (i == c) ? T(1) : T(0);
-            for (int q = c; q < i; ++q) s -= M[i + (size_t)q * ld] * Inv[q + (size_t)c * ld];
-            Inv[i + (size_t)c * ld] = s;
-        }
+    // U1^{-1} (unit lower) by column-sweep forward substitution: Inv = I; for
+    // q = 0 .. b-1: rows i > q lose U1[i,q] times row q (columns c <= q).
+    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
+        const int i = idx % b, c = idx / b;
+        Inv[i + (size_t)c * ld] = i == c ? T(1) : T(0);
     }
     __syncthreads();
-    // T = -W1 S U1^{-T}: T[a, c] = -sum_{q=a..c} W1[a,q] S_q U1inv[c,q]
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-        const int a = idx % b, c = idx / b;
-        T s = 0;
-        for (int q = a; q <= c; ++q) s += M[a + (size_t)q * ld] * Sg[q] * Inv[c + (size_t)q * ld];
-        Tm[a + (size_t)c * b] = a <= c ? -s : T(0);
+    for (int q = 0; q < b - 1; ++q) {
+        const int h = b - 1 - q, w = q + 1;
+        for (int idx = threadIdx.x; idx < h * w; idx += blockDim.x) {
+            const int i = q + 1 + idx % h, c = idx / h;
+            Inv[i + (size_t)c * ld] -= M[i + (size_t)q * ld] * Inv[q + (size_t)c * ld];
+        }
+        __syncthreads();
     }
+    // T = -(W1 S) U1^{-T} (upper: the product of the two triangular factors)
+    cta_gemm<T, false, true>(b, b, b, T(-1), WS, ld, Inv, ld, T(0), Tm, b);
 }
 
 // U[b:N, :] = Q[b:N, :] W1^{-1}; also zeroes the panel of A below its top b
@@ -488,7 +493,7 @@ int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws)
     const int cs = plan.cs;
     if (smem_leaf_qr<T>(r_leaf, b) > h->smem_optin || smem_node_qr<T>(F, b) > h->smem_optin ||
         smem_leaf_apply<T>(r_leaf, b, cs) > h->smem_optin || smem_node_apply<T>(F, b, cs) > h->smem_optin ||
-        sizeof(T) * (2 * (size_t)(b + 1) * b + b) > h->smem_optin)
+        sizeof(T) * (3 * (size_t)(b + 1) * b + b) > h->smem_optin)
         return SEV_ERR_UNSUPPORTED;
 
     const size_t s_leaf = smem_leaf_qr<T>(r_leaf, b);
@@ -535,7 +540,7 @@ int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws)
                cs, B.Yleaf, N, B.tau, B.nref, B.Zbuf, B.Q, N, B.Tbuf);
     // reconstruction
     const T *Rroot = B.Rbuf + (size_t)(plan.total - 1) * b * b;
-    const size_t s_lu = sizeof(T) * (2 * (size_t)(b + 1) * b + b);
+    const size_t s_lu = sizeof(T) * (3 * (size_t)(b + 1) * b + b);
     SEV_CUDA(cudaFuncSetAttribute(recon_lu_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_lu));
     SEV_LAUNCH(h, K_RECON_LU, recon_lu_kernel<T>, 1, kThreads, s_lu, b, B.Q, N, Rroot, U, N, Tm, B.Winv, P, lda);
     const size_t s_u2 = sizeof(T) * (size_t)(b + 1) * b;
