@@ -211,6 +211,18 @@ int sev_eigvalsh_batched(sev_handle handle, int count, const int *n, const int *
  */
 int sev_batch_autotune(sev_handle handle, int count, const int *n, int prec, int *b_best);
 
+/*
+ * The band widths sev_eigvalsh goes through for an n x n matrix (host only,
+ * no device work): bands[0] = b0 (0 picks the default for (n, prec), and
+ * b0 is clamped to n - 1), then every band-to-band stage's target width, the
+ * last being 1 (Algorithm 4.3 with the stage widths of this library: a band
+ * of width <= 16 goes straight to 1, one of 128 or more first to 32, other
+ * multiples of 16 to 16).  Returns the number of widths written (0 for
+ * n <= 1) or -5 if max_bands is too small; other negative values name the
+ * invalid argument (n = 1, b0 = 2, prec = 3, bands = 4).
+ */
+int sev_band_schedule(int n, int b0, int prec, int *bands, int max_bands);
+
 /* Copy the diagonal and first subdiagonal of a packed band (float or double
  * by prec) into FP64 device arrays d (n) and e (n-1). */
 int sev_band_tridiag_extract(sev_handle handle, int n, const void *AB, int ldab, int prec, double *d,

@@ -56,6 +56,7 @@ SIGNATURES = {
                                   ctypes.POINTER(_vp)]),
     "sev_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
     "sev_diag_house_scalars": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "sev_band_schedule": (_i, [_i, _i, _i, ctypes.POINTER(_i), _i]),
 }
 
 _lib = None

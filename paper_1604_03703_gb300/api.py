@@ -247,6 +247,15 @@ class BatchPlan:
             pass
 
 
+def band_schedule(n: int, b0: int = 0, prec: int = _lib.SEV_MIXED) -> list:
+    """Band widths sev_eigvalsh goes through (b0, ..., 1); host only."""
+    lib = _lib.load()
+    buf = (ctypes.c_int * 40)()
+    k = lib.sev_band_schedule(n, b0, prec, buf, 40)
+    check(k if k < 0 else 0, "sev_band_schedule")
+    return [buf[i] for i in range(k)]
+
+
 _default = {}
 
 

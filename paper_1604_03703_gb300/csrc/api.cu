@@ -654,6 +654,21 @@ int sev_batch_autotune(sev_handle h, int count, const int *n, int prec, int *b_b
     return SEV_OK;
 }
 
+int sev_band_schedule(int n, int b0, int prec, int *bands, int max_bands) {
+    if (n < 0) return -1;
+    if (b0 < 0) return -2;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -3;
+    if (!bands) return -4;
+    if (n <= 1) return 0;
+    if (b0 == 0) b0 = default_b0(n, prec);
+    if (b0 > n - 1) b0 = n - 1 > 1 ? n - 1 : 1;
+    int sched[40];
+    const int ns = schedule(b0, prec == SEV_FP64 ? 8 : 4, sched);
+    if (ns > max_bands) return -5;
+    for (int k = 0; k < ns; ++k) bands[k] = sched[k];
+    return ns;
+}
+
 int sev_get_error(sev_handle h) {
     if (!h) return -1;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return SEV_ERR_CUDA;

@@ -64,3 +64,23 @@ def test_product_never_imports_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+def test_band_schedule_host_query(lib):
+    """The host-only schedule query: stage widths of the library (and the
+    mirror the benchmark uses to name its workload agree with it)."""
+    import bench
+    from paper_1604_03703_gb300 import api, _lib as L
+
+    assert api.band_schedule(16384, 128, L.SEV_MIXED) == [128, 32, 16, 1]
+    assert api.band_schedule(16384, 64, L.SEV_MIXED) == [64, 16, 1]
+    assert api.band_schedule(16384, 0, L.SEV_MIXED) == [64, 16, 1]  # default b0
+    assert api.band_schedule(512, 32, L.SEV_FP64) == [32, 16, 1]
+    assert api.band_schedule(10, 64, L.SEV_FP64) == [9, 1]  # b0 clamped to n - 1
+    assert api.band_schedule(1, 8, L.SEV_FP64) == []
+    for b0 in (2, 4, 8, 16, 24, 32, 48, 64, 96, 128, 256):
+        for prec, elem in ((L.SEV_MIXED, 4), (L.SEV_FP64, 8)):
+            assert api.band_schedule(100000, b0, prec) == bench.schedule(b0, elem), (b0, prec)
+    buf = (__import__("ctypes").c_int * 2)()
+    assert lib.sev_band_schedule(16384, 128, L.SEV_MIXED, buf, 2) == -5
+    assert lib.sev_band_schedule(-1, 8, L.SEV_MIXED, buf, 2) == -1
