@@ -1,0 +1,46 @@
+"""Host-side pieces of the benchmark (no GPU): the work models behind the
+roofline object, the roofline arithmetic, and the oracle sample of the CPU
+baseline on a small matrix."""
+import math
+
+import numpy as np
+import pytest
+
+import bench
+from paper_1604_03703_gb300 import inputs as I
+
+
+def test_panel_sizes_and_flops():
+    n, b = 1024, 128
+    Ns = bench.panel_sizes(n, b)
+    assert Ns[0] == n - b and all(N >= 2 for N in Ns)
+    assert len(Ns) == math.ceil(n / b) - 1
+    amount, unit, bound = bench.kernel_model("syr2k_tc", n, b, 4)
+    assert unit == "flop" and bound == "tensor"
+    assert amount == pytest.approx(sum(2.0 * N * (N + 1) * b for N in Ns))
+
+
+def test_band_models_follow_the_schedule():
+    n = 4096
+    tri, unit, bound = bench.kernel_model("band_tri", n, 128, 4)
+    assert unit == "byte" and bound == "hbm"
+    assert tri == pytest.approx(2 * 4 * 16 * n ** 2)  # last stage 16 -> 1
+    chase, _, _ = bench.kernel_model("band_chase", n, 128, 4)
+    # 128 -> 32 (k = 4) and 32 -> 16 (k = 2)
+    assert chase == pytest.approx(2 * 4 * (4 + 2) * n ** 2)
+
+
+def test_roofline_arithmetic():
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1500.0}
+    r = bench.roofline("band_chase", 3.0e9, "byte", "hbm", 1000.0, peaks, {"sm_mhz": 2000.0}, 4)
+    assert r["bound"] == "hbm" and r["achieved"] == pytest.approx(3.0)
+    assert r["frac"] == pytest.approx(3.0 / 6000.0)
+    t = bench.roofline("syr2k_tc", 5.0e12, "flop", "tensor", 100.0, peaks, None, 4)
+    assert t["peak"] == pytest.approx(500.0) and t["achieved"] == pytest.approx(50.0)
+
+
+def test_oracle_sample_extrapolates(orc):
+    A = I.semicircle(96, 3)
+    r = bench.oracle_sample(A, 96, 1e-9, 0.2)
+    assert r["seconds_extrapolated"] > 0 and r["value"] > 0
+    assert "Householder steps" in r["sample"]
