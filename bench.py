@@ -176,9 +176,9 @@ def kernel_model(name, n, b0, elem):
     if name in ("syr2k", "syr2k_tc"):
         flops = sum(2.0 * N * (N + 1) * b0 for N in Ns)
         return flops, "flop", "tensor" if name.endswith("_tc") else "alu"
-    if name in ("symm", "symm_tc"):
+    if name == "symm":
         flops = sum(2.0 * N * N * b0 for N in Ns)
-        return flops, "flop", "tensor" if name.endswith("_tc") else "alu"
+        return flops, "flop", "alu"
     if name == "band_tri":
         b1 = sched[-2]
         return 2.0 * elem * b1 * float(n) ** 2, "byte", "hbm"

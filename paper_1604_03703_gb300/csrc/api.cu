@@ -17,8 +17,8 @@ const char *const kKernelNames[K_COUNT] = {
     "bisect_prep",  "bisect",       "band_from_dense", "tridiag_extract", "band_chase", "band_tri",
     "tsqr_leaf_qr", "tsqr_node_qr", "tsqr_node_apply", "tsqr_leaf_apply", "recon_lu",
     "recon_u2",     "symm",         "vform_xt",        "vform_utx",       "vform_reduce",
-    "vform_v",      "syr2k",        "split_bf16",      "syr2k_tc",        "symm_tc",
-    "batch",        "misc"};
+    "vform_v",      "syr2k",        "split_bf16",      "syr2k_tc",        "batch",
+    "misc"};
 
 static cudaEvent_t pool_get(sev_ctx *h) {
     if (!h->event_pool.empty()) {

@@ -37,7 +37,6 @@ enum KernelId {
     K_SYR2K,
     K_SPLIT_BF16,
     K_SYR2K_TC,
-    K_SYMM_TC,
     K_BATCH,
     K_MISC,
     K_COUNT

@@ -9,9 +9,9 @@
 //   V  = 1/2 U Zm - X                (the V_1 line of Algorithm 4.1)
 //   A22 <- A22 + U V^T + V U^T       (syr2k, lower tiles only)
 //
-// These SIMT kernels (64 x 64 output tiles, 4 x 4 per thread, FMA on the
-// CUDA cores) run the FP64 form at the FP64 pipe's rate; the mixed form's
-// symm and syr2k use the tensor-core kernels of update_tc.cu.
+// The FP64 form runs all of it on SIMT tiles (64 x 64 outputs, 4 x 4 per
+// thread, DFMA); the mixed form's symm runs on larger FP32 tiles
+// (symm_f32_kernel) and its syr2k on the tensor cores (update_tc.cu).
 #include "common.cuh"
 
 namespace sev {
@@ -22,8 +22,6 @@ template <typename T>
 size_t panel_workspace(sev_ctx *h, int n, int b);
 template <typename T>
 int tc_update_supported(sev_ctx *h, int N, int b);
-template <typename T>
-int tc_symm(sev_ctx *h, int N, int b, const T *A22, int lda, const T *U, T *Y, void *ws);
 template <typename T>
 int tc_syr2k(sev_ctx *h, int N, int b, T *A22, int lda, const T *U, const T *V, void *ws);
 template <typename T>
@@ -479,12 +477,8 @@ int launch_full_to_band(sev_ctx *h, int n, T *A, int lda, int b, T *AB, int ldab
         int rc = panel_factor<T>(h, N, b, P, lda, B.U, B.Tm, B.panel_ws);
         if (rc) return rc;
         const bool tc = tc_update_supported<T>(h, N, b);
-        const bool tc_symm_ok = false;  // the symmetric product still runs on the SIMT tiles
         // Y = A22 U
-        if (tc_symm_ok) {
-            rc = tc_symm<T>(h, N, b, A22, lda, B.U, B.Y, B.tc_ws);
-            if (rc) return rc;
-        } else if (sizeof(T) == 4 && lda % 4 == 0 && ((uintptr_t)A22 & 15) == 0) {
+        if (sizeof(T) == 4 && lda % 4 == 0 && ((uintptr_t)A22 & 15) == 0) {
             // split K until the grid covers ~2 CTAs per SM
             const int mt = (N + SBM - 1) / SBM, nt = (b + SBN - 1) / SBN;
             int splits = 1;

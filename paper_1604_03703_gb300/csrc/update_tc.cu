@@ -341,15 +341,8 @@ int tc_syr2k(sev_ctx *h, int N, int b, T *A22, int lda, const T *U, const T *V, 
     }
 }
 
-template <typename T>
-int tc_symm(sev_ctx *, int, int, const T *, int, const T *, T *, void *) {
-    return SEV_ERR_UNSUPPORTED;
-}
-
 template int tc_update_supported<float>(sev_ctx *, int, int);
 template int tc_update_supported<double>(sev_ctx *, int, int);
-template int tc_symm<float>(sev_ctx *, int, int, const float *, int, const float *, float *, void *);
-template int tc_symm<double>(sev_ctx *, int, int, const double *, int, const double *, double *, void *);
 template int tc_syr2k<float>(sev_ctx *, int, int, float *, int, const float *, const float *, void *);
 template int tc_syr2k<double>(sev_ctx *, int, int, double *, int, const double *, const double *, void *);
 template size_t tc_workspace<float>(int, int);
