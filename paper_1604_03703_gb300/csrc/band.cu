@@ -14,7 +14,8 @@
 // symmetric rank-2 update U V^T + V U^T.
 //
 // Schedule.  A CTA takes sweeps i in increasing order (global counter) and
-// runs its chases j = 1, 2, ...; chase (i, j) waits until sweep i-1 has
+// runs its chases j = 1, 2, ... (the grid is capped to the ~J/3 sweeps that
+// can progress together); chase (i, j) waits until sweep i-1 has
 // completed chase j+2 (or all of its chases).  Chase (i, j) overlaps chase
 // (i-1, j+2) -- its bulge rows [o+2b-h, o+2b) are the rows that (i-1, j+2)
 // factorises -- so the pipeline t = 2i + j that the Fig. 2 caption pictures

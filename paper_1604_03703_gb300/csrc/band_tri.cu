@@ -11,20 +11,21 @@
 // the qr rows; off rows get X <- X H (row-local), the qr-row block gets
 // H X H = X - v w^T - w v^T with p = tau X v, w = p - (tau/2)(p^T v) v.
 //
-// Schedule.  A CTA takes G consecutive sweeps (warp g -> sweep i0 + g) and
-// steps them together: at step t warp g performs chase t - 3g, so sweep i
-// runs 3 chases behind sweep i - 1 -- the rule that chase (i, j) follows
-// (i - 1, j + 2) -- and the chases of one step are independent.  Steps are
-// separated by __syncthreads.  The band columns the group touches live in a
-// shared-memory ring of (3G + 1) b + 2 columns (2b diagonals each): columns
-// are loaded from global memory as warp 0 reaches them and written back
+// Schedule.  A CTA takes G consecutive sweeps (compute warp g -> sweep
+// i0 + g) and steps them together: at step t warp g performs chase t - 3g,
+// so sweep i runs 3 chases behind sweep i - 1 -- the rule that chase (i, j)
+// follows (i - 1, j + 2) -- and the chases of one step are independent.
+// Steps are separated by a named barrier among the compute warps.  The band
+// columns the group touches live in a shared-memory ring of (3G + 3) b + 2
+// columns (2b diagonals each): a loader warp brings columns in (16-byte
+// asynchronous copies) ahead of warp 0, and a writer warp writes them back
 // once the group's last sweep has passed them (after its chase j, columns
-// below o_qr.r(i_last, j) are final).  The group then publishes j with a
-// release store; the next group waits (acquire, capped) for j + 2 before
-// loading a column range -- the only global synchronisation, once per step
-// per group boundary.  Groups are handed out in order by a global counter
-// and each CTA finishes its group before taking another, so every awaited
-// group is held by a running CTA.
+// below o_qr.r(i_last, j) are final).  The writer then publishes j with a
+// release store; the next group's loader waits (acquire, capped) for j + 2
+// before loading a column range -- the only global synchronisation, once
+// per step per group boundary.  Groups are handed out in order by a global
+// counter and each CTA finishes its group before taking another, so every
+// awaited group is held by a running CTA.
 #include "common.cuh"
 
 #ifdef SEV_TRACE
