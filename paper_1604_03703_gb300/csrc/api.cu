@@ -1,7 +1,8 @@
 // api.cu -- the C ABI (include/sev.h): handle, workspace, argument checks,
 // per-kernel timing, and the eigvalsh driver that chains the stages of
-// Algorithm 4.3: full-to-band, band halvings b0 -> b0/2 -> ... -> 1, and
-// bisection on the final tridiagonal.
+// Algorithm 4.3: full-to-band, band-to-band stages b0 -> ... -> 1 (the stage
+// widths come from schedule() below), and bisection on the final
+// tridiagonal.
 #include <cstdlib>
 #include <cstring>
 #include <new>

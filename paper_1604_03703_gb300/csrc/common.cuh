@@ -463,9 +463,11 @@ __device__ __forceinline__ void warp_apply_house_f32(int m, int k, const float *
 
 // Householder QR of the m x nc block P (shared memory, column-major, ld):
 // r = min(nc, m-1) reflectors.  At step k the warp `own` = (k+1) mod nw
-// applies H_k to column k+1 and forms reflector k+1 (lookahead) -- and
-// nothing else, so the reflector's FP64 chain is the whole of its work --
-// while the other warps apply H_k to columns k+2.. , four at a time.  One
+// applies H_k to column k+1 and forms reflector k+1 (lookahead) and nothing
+// else, keeping the serial per-column chain short (FP32 with m-k <= 256: the
+// fused register-resident warp_apply_house_f32 with pair-float scalars;
+// otherwise warp_apply2 then warp_house), while the other warps apply H_k
+// to columns k+2.. , four at a time.  One
 // __syncthreads per step.  On return R is in the upper trapezoid, the
 // Householder vectors below the diagonal (unit diagonal implicit) and
 // tau[0..r-1] holds the scalars.  Returns r.
