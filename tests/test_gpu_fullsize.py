@@ -70,19 +70,33 @@ def test_bisect_n16384_sampled_bitwise(H, torch_cuda, orc, rtol, kind):
 
 
 # --------------------------------------------------------------- band stages
-@pytest.mark.parametrize("dtype_name,b0,mid", [("float32", 128, 32), ("float64", 64, 16)])
-def test_band_stages_n16384_inertia(H, torch_cuda, orc, dtype_name, b0, mid):
-    """The band schedule of the benchmark (b0 -> mid -> 1) at n = 16384 on a
-    random band matrix: the tridiagonal's Sturm counts equal the inertia of
-    the input band at shifts away from its eigenvalues."""
+@pytest.mark.parametrize(
+    "dtype_name,b0,mids",
+    [("float32", 128, None), ("float64", 64, None), ("float32", 128, [32])],
+    ids=["fp32-schedule", "fp64-schedule", "fp32-128-32-1"],
+)
+def test_band_stages_n16384_inertia(H, torch_cuda, orc, dtype_name, b0, mids):
+    """Band stages at n = 16384 on a random band matrix: the library's own
+    schedule (mids None: 128 -> 32 -> 16 -> 1 mixed, 64 -> 16 -> 1 FP64, the
+    calls eigvalsh makes) and 128 -> 32 -> 1 (the b -> 1 kernel at b = 32).
+    The tridiagonal's Sturm counts equal the inertia of the input band at
+    shifts away from its eigenvalues."""
     torch = torch_cuda
+    from paper_1604_03703_gb300 import api, _lib as L
+
     dtype = getattr(torch, dtype_name)
     n, ldab = 16384, 2 * b0
+    if mids is None:
+        prec = L.SEV_MIXED if dtype_name == "float32" else L.SEV_FP64
+        widths = api.band_schedule(n, b0, prec)
+    else:
+        widths = [b0] + list(mids) + [1]
+    assert widths[0] == b0 and widths[-1] == 1
     AB = I.random_band_packed(n, b0, ldab, 9200 + b0)
     AB_t = torch.from_numpy(np.ascontiguousarray(AB.T)).to(dtype).cuda()
     AB = AB_t.double().cpu().numpy().T.copy()  # the exact input the GPU sees
-    H.band_to_band(AB_t, b0, mid)
-    H.band_to_band(AB_t, mid, 1)
+    for b, h in zip(widths[:-1], widths[1:]):
+        H.band_to_band(AB_t, b, h)
     d_t, e_t = H.band_tridiag(AB_t)
     torch.cuda.synchronize()
     H.raise_device_error("band stages")
