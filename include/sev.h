@@ -28,8 +28,11 @@
  *  - Precision: SEV_FP64 -- data double, all arithmetic FP64.
  *    SEV_MIXED -- data float (FP32); the trailing update runs as BF16x3
  *    split products on the tensor cores with FP32 accumulation; Householder
- *    norms, tau and beta are computed in FP64; the Sturm recurrence of the
- *    bisection is FP64; eigenvalues are returned as double.
+ *    norms, tau and beta are FP64-accurate (sums of squares accumulated
+ *    error-free as pairs of floats, the scalars evaluated in pair-float
+ *    arithmetic; they equal the FP64 evaluation rounded to float, which
+ *    sev_diag_house_scalars lets a caller check); the Sturm recurrence of
+ *    the bisection is FP64; eigenvalues are returned as double.
  *  - Return codes: SEV_OK = 0; a negative value -i means argument i (1-based,
  *    the handle counts as argument 1) is invalid; positive values are the
  *    SEV_ERR_* codes below.
@@ -53,7 +56,7 @@ typedef struct sev_ctx *sev_handle;
 
 typedef enum {
     SEV_FP64 = 0,  /* double data, FP64 arithmetic throughout */
-    SEV_MIXED = 1  /* float data, BF16x3 tensor-core update, FP64 norms/tau/beta and Sturm */
+    SEV_MIXED = 1  /* float data, BF16x3 tensor-core update, FP64-accurate norms/tau/beta, FP64 Sturm */
 } sev_prec;
 
 enum {
@@ -90,8 +93,8 @@ int sev_set_workspace(sev_handle handle, void *workspace, size_t bytes);
 /*
  * Eigenvalues of the symmetric n x n matrix A (Algorithm 4.3):
  * full-to-band to half-bandwidth b0, band-to-band stages down to the
- * tridiagonal (b0 -> w -> 1, w the widest of 32 (16 in FP64), 16, 8, 4, 2
- * that divides b0; straight to 1 from b0 <= 32), bisection.
+ * tridiagonal with the widths sev_band_schedule reports (e.g. 128 -> 32 ->
+ * 16 -> 1, 64 -> 16 -> 1, 16 -> 1), bisection.
  *   A      device, n x n, leading dimension lda >= max(1, n); double for
  *          SEV_FP64, float for SEV_MIXED; lower triangle read, overwritten.
  *   b0     first half-bandwidth, 1 <= b0 (values >= n-1 skip full-to-band);

@@ -172,7 +172,7 @@ def test_full_to_band_fp32_vs_oracle(H, torch_cuda, orc, n, b):
 
 # --------------------------------------------------------------- end to end
 def test_eigvalsh_qdq512_fp64(H, torch_cuda, orc):
-    """n = 512, A = Q diag(linspace(-1, 1)) Q^T, b0 = 32: halvings 32 -> ... -> 1."""
+    """n = 512, A = Q diag(linspace(-1, 1)) Q^T, b0 = 32: stages 32 -> 16 -> 1."""
     torch = torch_cuda
     A, D = I.workload_qdq512()
     ref = orc.eigvalsh(A, 1e-14)
