@@ -243,11 +243,21 @@ __global__ void __launch_bounds__(128, 1)
             float acc[32];
             tmem_ld32(tbase + cc * 32, acc);
             if (row < N) {
+                // All 32 loads are issued before any store: the compiler cannot
+                // prove arow[j * lda] distinct across j (lda is a runtime
+                // value), so a fused load-add-store loop would wait one memory
+                // latency per column.
                 float *arow = A + row;
+                float old[32];
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {
                     const int j = J * 128 + cc * 32 + c;
-                    if (j < N && row >= j) arow[(size_t)j * lda] += acc[c];
+                    old[c] = (j < N && row >= j) ? arow[(size_t)j * lda] : 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const int j = J * 128 + cc * 32 + c;
+                    if (j < N && row >= j) arow[(size_t)j * lda] = old[c] + acc[c];
                 }
             }
         }
