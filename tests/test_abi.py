@@ -84,3 +84,33 @@ def test_band_schedule_host_query(lib):
     buf = (__import__("ctypes").c_int * 2)()
     assert lib.sev_band_schedule(16384, 128, L.SEV_MIXED, buf, 2) == -5
     assert lib.sev_band_schedule(-1, 8, L.SEV_MIXED, buf, 2) == -1
+
+
+def test_missing_library_fails_loudly():
+    """Without the built library the binding raises; nothing falls back to
+    the CPU (fresh interpreter, since a loaded library is cached)."""
+    import subprocess
+    import sys
+
+    code = (
+        "from paper_1604_03703_gb300 import _lib\n"
+        "try:\n"
+        "    _lib.load('/nonexistent/libsev.so')\n"
+        "except RuntimeError as e:\n"
+        "    assert 'no CPU fallback' in str(e), e\n"
+        "    print('raised')\n"
+    )
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0 and out.stdout.strip() == "raised", out.stderr
+
+
+def test_status_errors_are_raised(lib):
+    from paper_1604_03703_gb300 import _lib as L
+
+    with pytest.raises(L.SevError) as ei:
+        L.check(3, "probe")  # SEV_ERR_TIMEOUT
+    assert ei.value.code == 3 and "probe" in str(ei.value)
+    with pytest.raises(L.SevError) as ei:
+        L.check(-4, "probe")
+    assert "argument 4" in str(ei.value)
+    L.check(0, "probe")
