@@ -584,10 +584,12 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+bf16x3 (f64 norms, f64 Sturm)", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+bf16x3+f64", "data": "synthetic",
         "config": {"workload": "eigvalsh n=%d, A = Q diag(D) Q^T, D geometric 1e-6..1 with random signs and "
                                "16-fold clusters (gap 1e-10), FP32 data, bands %s" % (n, "->".join(map(str, schedule(b0, 4)))),
                    "n": n, "b0": b0, "schedule": schedule(b0, 4), "parallelism": "replicas" if world > 1 else "single",
+                   "precision": "mixed: FP32 data and FP32 arithmetic, BF16x3 tensor-core trailing update "
+                                "(FP32 accumulation), pair-float Householder scalars, FP64 Sturm counts",
                    "l2": "inputs larger than L2 (1 GiB matrix per step); input restore excluded from step events"},
         "max_err_vs_D": err,
         "e2e": e2e,
