@@ -114,7 +114,10 @@ def test_band_stages_n16384_inertia(H, torch_cuda, orc, dtype_name, b0, mids):
     delta = (3e-5 if dtype_name == "float32" else 1e-9) * radius
     rng = np.random.default_rng(9300 + b0)
     xs = rng.uniform(-0.8, 0.8, 16) * radius
-    for x, want in clean_shifts(lambda t: orc.band_inertia(AB, b0, t), xs, delta):
+    # (the banded LDL^T runs in long double: software quad precision on some
+    # hosts, seconds per shift at b = 128, so the extra route checks 2 shifts)
+    shifts = clean_shifts(lambda t: orc.band_inertia(AB, b0, t), xs, delta, want=4 if mids is None else 2)
+    for x, want in shifts:
         assert orc.sturm_count(d, e, x) == want
 
 
