@@ -65,6 +65,8 @@ def _load():
             lib.orc_bisect.argtypes = [i, _dp, _dp, d, i, _dp]
             lib.orc_bisect_range.restype = i
             lib.orc_bisect_range.argtypes = [i, _dp, _dp, d, i, i, i, _dp]
+            lib.orc_bisect_ldlt.restype = i
+            lib.orc_bisect_ldlt.argtypes = [i, _dp, _dp, d, i, i, ctypes.POINTER(ctypes.c_int), _dp]
             lib.orc_eigvalsh.restype = i
             lib.orc_eigvalsh.argtypes = [i, _dp, i, d, _dp]
             lib.orc_jacobi.restype = i
@@ -177,6 +179,22 @@ def bisect_range(d, e, k0: int, k1: int, rtol: float = 1e-14, maxit: int = 200):
     out = np.zeros(max(k1 - k0, 1))
     _load().orc_bisect_range(n, _ptr(d), _ptr(ee), float(rtol), int(maxit), int(k0), int(k1), _ptr(out))
     return out[: k1 - k0]
+
+
+def bisect_ldlt(d, e, rtol: float = 1e-14, idx=None, maxit: int = 200, return_noconv: bool = False):
+    """Eigenvalues of T(d, e) with indices ``idx`` (0-based ascending order;
+    all n when None) by plain bisection on the LDL^T pivot count with the
+    pivmin guard from the unscaled Gershgorin interval -- the textbook
+    definition, independent of ``bisect``'s minors count and rescaling."""
+    d = np.ascontiguousarray(d, dtype=np.float64)
+    n = d.size
+    ee = np.zeros(max(n, 1))
+    ee[: n - 1] = np.asarray(e, dtype=np.float64)[: n - 1]
+    ix = np.arange(n, dtype=np.intc) if idx is None else np.ascontiguousarray(idx, dtype=np.intc)
+    out = np.zeros(max(ix.size, 1))
+    nc = _load().orc_bisect_ldlt(n, _ptr(d), _ptr(ee), float(rtol), int(maxit), int(ix.size),
+                                 ix.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), _ptr(out))
+    return (out[: ix.size], nc) if return_noconv else out[: ix.size]
 
 
 def eigvalsh(A, rtol: float = 1e-14):

@@ -369,6 +369,62 @@ int orc_bisect_range(int n, const double *d, const double *e, double rtol, int m
     return noconv;
 }
 
+/*
+ * Textbook Sturm bisection on the LDL^T pivot count (the final eigenvalue
+ * step of Algorithm 4.3, by the method the eigenvalue step is defined with:
+ * bisection on Sturm counts), written without any of the rescaling,
+ * division-free or exponent tricks of orc_bisect, as an independent second
+ * definition of the same result:
+ *   pivmin = orc_pivmin(e);  [lo, hi] = orc_gershgorin(d, e) (unscaled,
+ *   widened by 2 n eps ||T|| + 4 pivmin);  count(x) = orc_sturm_count (q_0 =
+ *   d_0 - x, q_i = (d_i - x) - e_{i-1}^2 / q_{i-1}, |q_i| < pivmin -> -pivmin,
+ *   negative q counted);  mid = (lo + hi)/2;  count(mid) >= k+1 -> hi = mid
+ *   else lo = mid;  stop when hi - lo <= max(rtol max(|lo|,|hi|), rtol ||T||_G)
+ *   or after maxit steps (or once mid no longer splits the interval);
+ *   eigenvalue k = (lo + hi)/2.
+ * For each of the nidx indices idx[m] (0-based, the (idx[m]+1)-th smallest)
+ * the result goes to eigs[m].  Returns the number that hit maxit.
+ */
+int orc_bisect_ldlt(int n, const double *d, const double *e, double rtol, int maxit, int nidx, const int *idx,
+                    double *eigs)
+{
+    if (n <= 0) return 0;
+    if (n == 1) {
+        for (int m = 0; m < nidx; ++m) eigs[m] = d[0];
+        return 0;
+    }
+    double *e2 = (double *)malloc(sizeof(double) * (size_t)n);
+    for (int i = 0; i + 1 < n; ++i) e2[i] = e[i] * e[i];
+    e2[n - 1] = 0.0;
+    double pm = orc_pivmin(n, e);
+    double gl, gu;
+    double tnorm = orc_gershgorin(n, d, e, pm, &gl, &gu);
+    double atol = rtol * tnorm;
+    int noconv = 0;
+    for (int m = 0; m < nidx; ++m) {
+        int k = idx[m];
+        double lo = gl, hi = gu;
+        for (int it = 0;; ++it) {
+            double mag = fabs(lo) > fabs(hi) ? fabs(lo) : fabs(hi);
+            double tol = rtol * mag > atol ? rtol * mag : atol;
+            if (hi - lo <= tol) break;
+            if (it >= maxit) {
+                ++noconv;
+                break;
+            }
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi) break;
+            if (orc_sturm_count(n, d, e2, mid, pm) >= k + 1)
+                hi = mid;
+            else
+                lo = mid;
+        }
+        eigs[m] = 0.5 * (lo + hi);
+    }
+    free(e2);
+    return noconv;
+}
+
 /* Eigenvalues of the symmetric A (lower triangle), ascending: tridiagonalise
  * then bisect (the composite result of Algorithm 4.3).  A is overwritten. */
 int orc_eigvalsh(int n, double *A, int lda, double rtol, double *eigs)

@@ -116,6 +116,64 @@ def test_bisect_tolerance_respected(orc):
         assert np.abs(got - lam).max() <= rtol * tn + 1e-13 * tn
 
 
+# ------------------------------------- textbook LDL^T bisection (O3 form)
+def test_bisect_ldlt_golden(orc):
+    for line in open(os.path.join(GOLD, "tridiag_closed_forms.txt")):
+        if not line.strip() or line[0] == "#":
+            continue
+        f = [s.strip() for s in line.split("|")]
+        n = int(f[0])
+        d = np.array(f[1].split(), dtype=float)
+        e = np.array(f[2].split(), dtype=float) if f[2] else np.zeros(0)
+        lam = np.array(f[3].split(), dtype=float)
+        got = orc.bisect_ldlt(d, e, 1e-15)
+        assert got.shape == (n,)
+        np.testing.assert_allclose(got, lam, atol=4e-15 * max(1, np.abs(lam).max()))
+
+
+@pytest.mark.parametrize("n,a,b", [(1, 0.3, 0.0), (2, 1.0, 2.0), (10, 2.0, -1.0), (100, 0.0, 1.0), (513, -3.0, 0.25)])
+def test_bisect_ldlt_toeplitz_closed_form(orc, n, a, b):
+    d, e, lam = I.toeplitz(n, a, b)
+    got = orc.bisect_ldlt(d, e, 1e-14)
+    tn = abs(a) + 2 * abs(b)
+    np.testing.assert_allclose(got, lam, atol=max(4e-14 * tn, 1e-300), rtol=0)
+
+
+def test_bisect_ldlt_diagonal_split_and_signs(orc):
+    d = np.array([3.0, -1.0, 2.0, 2.0, 0.0])
+    np.testing.assert_allclose(orc.bisect_ldlt(d, np.zeros(4), 1e-15), np.sort(d), atol=1e-15)
+    d1, e1, l1 = I.toeplitz(4, 1.0, 0.5)
+    d2, e2, l2 = I.toeplitz(3, -2.0, 1.0)
+    got = orc.bisect_ldlt(np.concatenate([d1, d2]), np.concatenate([e1, [0.0], e2]), 1e-15)
+    np.testing.assert_allclose(got, np.sort(np.concatenate([l1, l2])), atol=2e-14)
+    # the spectrum depends on e only through e^2: flipping signs changes nothing
+    d, e = I.random_tridiagonal(80, 12)
+    s = np.where(I.rng(13).random(79) < 0.5, -1.0, 1.0)
+    np.testing.assert_array_equal(orc.bisect_ldlt(d, e * s, 1e-14), orc.bisect_ldlt(d, e, 1e-14))
+
+
+def test_bisect_ldlt_vs_library_and_subset(orc):
+    d, e = I.random_tridiagonal(300, 14)
+    lam = np.linalg.eigvalsh(np.diag(d) + np.diag(e, 1) + np.diag(e, -1))  # library routine
+    tn = orc.gershgorin(d, e)[2]
+    for rtol in [1e-6, 1e-10, 1e-14]:
+        got = orc.bisect_ldlt(d, e, rtol)
+        assert np.all(np.diff(got) >= 0)
+        assert np.abs(got - lam).max() <= rtol * tn + 1e-13 * tn
+    idx = np.array([299, 0, 150, 7])
+    np.testing.assert_array_equal(orc.bisect_ldlt(d, e, 1e-14, idx), orc.bisect_ldlt(d, e, 1e-14)[idx])
+
+
+def test_bisect_ldlt_clusters(orc):
+    # 16-fold clusters of gap 1e-10 around well separated centres, as in the
+    # clustered workload: every member resolved to the bisection tolerance
+    lam = np.concatenate([c + 1e-10 * np.arange(16) for c in (-0.75, -1e-3, 0.5)])
+    A = I.qdq(lam, 15)
+    d, e = orc.tridiagonalize(A)
+    got = orc.bisect_ldlt(d, e, 1e-14)
+    assert np.abs(got - np.sort(lam)).max() <= 1e-13
+
+
 # ----------------------------------------------------- cross-check routines
 def test_jacobi_closed_forms(orc):
     A = np.array([[1.0, 2.0], [2.0, 3.0]])
