@@ -12,19 +12,21 @@
  *   band-to-band    Algorithm 4.2 (bulge chasing, b -> h), repeated down
  *                   to the tridiagonal as in Algorithm 4.3
  *   tridiag_bisect  eigenvalues of the final tridiagonal by Sturm-count
- *                   bisection (the "compute its eigenvalues" step of
- *                   Algorithm 4.3)
+ *                   bisection (the last step of Algorithm 4.3, where the
+ *                   tridiagonal's eigenvalues are taken as the result)
  *
  * Conventions for every entry point:
  *  - Matrices are column-major.  Only the LOWER triangle of a symmetric input
- *    is read (the paper stores A "as a nonsymmetric matrix"; we read half).
+ *    is read (the paper's algorithms keep A in full storage, Sec. 4; the
+ *    upper triangle is never touched here).
  *  - Pointers are DEVICE pointers unless a name ends in _host.  The caller
  *    owns every buffer it passes; the library never frees them.
  *  - Inputs named A / AB are overwritten (LAPACK-style workspace semantics).
  *  - Calls are asynchronous on the handle's stream (sev_set_stream); a
  *    return of SEV_OK means the work was enqueued.  Errors detected on the
- *    device (a wait that timed out, a bisection that did not converge) are
- *    latched in the handle and returned by sev_get_error().
+ *    device (non-finite input, a wait that timed out, a bisection that did
+ *    not converge) are latched in the handle and returned by
+ *    sev_get_error().
  *  - Precision: SEV_FP64 -- data double, all arithmetic FP64.
  *    SEV_MIXED -- data float (FP32); the trailing update runs as BF16x3
  *    split products on the tensor cores with FP32 accumulation; Householder
@@ -102,6 +104,9 @@ int sev_set_workspace(sev_handle handle, void *workspace, size_t bytes);
  *   eigs   device, n doubles, ascending on completion.
  * Bisection tolerance: relative 1e-14 (SEV_FP64) or 1e-9 (SEV_MIXED) of the
  * Gershgorin bound of the tridiagonal.
+ * A NaN or Inf in A's lower triangle latches SEV_ERR_NONFINITE; the
+ * reductions still run over it (their work does not depend on the values),
+ * the bisection is skipped and eigs receives NaNs.
  */
 int sev_eigvalsh(sev_handle handle, int n, void *A, int lda, int b0, int prec, double *eigs);
 
@@ -119,6 +124,8 @@ int sev_eigvalsh_host(sev_handle handle, int n, const void *A_host, int lda, int
  * A22 <- A22 + U V^T + V U^T (Eq. 4.1), band block <- S R.
  *   A     device, n x n (lda), lower triangle read; on return A's lower
  *         triangle holds the band matrix (exact zeros below the band).
+ *         A NaN or Inf in it latches SEV_ERR_NONFINITE (the reduction still
+ *         runs; its output is then meaningless).
  *   b     half-bandwidth >= 1 (b >= n-1 only copies the band).
  *   AB    device, packed lower band, ldab >= b+1; receives the band matrix.
  */
@@ -160,11 +167,14 @@ int sev_tridiag_bisect(sev_handle handle, int n, const double *d, const double *
  *   rtol    1e-16 <= rtol < 1 (the bisection then always converges well
  *           inside its iteration cap, so no device-side status is needed)
  *   stream  cudaStream_t (as void*) on which the kernels are enqueued
- * The first call on each device looks up the array's device address (with
- * that device current); make that first call before any stream capture.
- * Every call on a device shares the one array, which keeps the last call's
- * contents: calls whose kernels overlap on the GPU (different streams
- * without ordering between them) race and must be serialised by the caller.
+ * Every call made outside stream capture looks up the array's device
+ * address on the current device (so the address stays right after a
+ * cudaDeviceReset); a call inside a capture uses the address found by the
+ * last call outside one, so make the first call on each device before any
+ * stream capture.  Every call on a device shares the one array, which keeps
+ * the last call's contents: calls whose kernels overlap on the GPU
+ * (different streams without ordering between them) race and must be
+ * serialised by the caller.
  */
 int sev_tridiag_bisect_static(int n, const double *d, const double *e, double rtol, double *eigs, void *stream);
 
@@ -245,6 +255,17 @@ int sev_diag_house_scalars(int count, const float *alpha, const float *ssq_hi, c
 /* Synchronise the handle's stream and return (and clear) the first error
  * latched by device code since the last call, or SEV_OK. */
 int sev_get_error(sev_handle handle);
+
+/*
+ * Time limit of every device-side wait of this handle's kernels (a sweep
+ * waiting on its predecessor's progress, a ring slot, an mbarrier, a grid
+ * barrier), in SM clock cycles; 0 restores the default of 4e9 (~2 s at
+ * 2 GHz).  A wait that runs out latches SEV_ERR_TIMEOUT and its kernel
+ * returns without finishing (the context stays usable).  Synchronises the
+ * handle's stream first.  A short limit is a watchdog for tests: work that
+ * legitimately waits longer than it then fails.  Negative cycles return -2.
+ */
+int sev_set_wait_limit(sev_handle handle, long long cycles);
 
 /* Human-readable text of a return code. */
 const char *sev_status_string(int code);

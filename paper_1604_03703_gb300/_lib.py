@@ -42,6 +42,7 @@ SIGNATURES = {
     "sev_band_tridiag_extract": (_i, [_vp, _i, _vp, _i, _i, _vp, _vp]),
     "sev_tridiag_bisect_static": (_i, [_i, _vp, _vp, _d, _vp, _vp]),
     "sev_get_error": (_i, [_vp]),
+    "sev_set_wait_limit": (_i, [_vp, ctypes.c_longlong]),
     "sev_status_string": (ctypes.c_char_p, [_i]),
     "sev_set_kernel_timing": (_i, [_vp, ctypes.c_ulonglong]),
     "sev_kernel_count": (_i, []),

@@ -179,6 +179,11 @@ class Handle:
     def raise_device_error(self, where: str = "device") -> None:
         check(self.get_error(), where)
 
+    def set_wait_limit(self, cycles: int = 0) -> None:
+        """Time limit of the handle's device-side waits in SM cycles (0: default)."""
+        self._sync_stream()
+        check(self._lib.sev_set_wait_limit(self._h, int(cycles)), "sev_set_wait_limit")
+
     # --------------------------------------------------------------- timing
     def set_kernel_timing(self, on=True) -> None:
         """True: time every kernel; False: none; a str or list of kernel

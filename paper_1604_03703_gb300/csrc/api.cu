@@ -3,6 +3,7 @@
 // Algorithm 4.3: full-to-band, band-to-band stages b0 -> ... -> 1 (the stage
 // widths come from schedule() below), and bisection on the final
 // tridiagonal.
+#include <cstddef>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -19,7 +20,7 @@ const char *const kKernelNames[K_COUNT] = {
     "tsqr_leaf_qr", "tsqr_node_qr", "tsqr_node_apply", "tsqr_leaf_apply", "recon_lu",
     "recon_u2",     "symm",         "vform_xt",        "vform_utx",       "vform_reduce",
     "vform_v",      "syr2k",        "split_bf16",      "syr2k_tc",        "batch",
-    "misc"};
+    "check_finite", "misc"};
 
 static cudaEvent_t pool_get(sev_ctx *h) {
     if (!h->event_pool.empty()) {
@@ -154,6 +155,7 @@ static size_t eig_workspace(sev_ctx *h, int n, int b0) {
     c.take<T>((size_t)ldab * n);
     c.take<double>((size_t)n);
     c.take<double>((size_t)n);
+    c.take<int>(1);
     c.take<char>(stage);
     return c.bytes();
 }
@@ -176,8 +178,15 @@ static int eigvalsh_t(sev_ctx *h, int n, T *A, int lda, int b0, double *eigs) {
     T *AB = c.take<T>((size_t)ldab * n);
     double *d = c.take<double>((size_t)n);
     double *e = c.take<double>((size_t)n);
+    int *nonfinite = c.take<int>(1);
     const size_t stage_bytes = need - c.bytes();
     void *stage = c.take<char>(stage_bytes);
+    // non-finite input: latch SEV_ERR_NONFINITE; the reductions still run
+    // (bounded work, no data-dependent control flow) and the bisection,
+    // whose step count depends on the data, is skipped (NaN eigenvalues)
+    SEV_CUDA(cudaMemsetAsync(nonfinite, 0, sizeof(int), h->stream));
+    rc = launch_check_finite<T>(h, n, A, lda, nonfinite);
+    if (rc) return rc;
     if (b0 < n - 1) {
         rc = launch_full_to_band<T>(h, n, A, lda, b0, AB, ldab, stage, stage_bytes);
     } else {
@@ -191,7 +200,7 @@ static int eigvalsh_t(sev_ctx *h, int n, T *A, int lda, int b0, double *eigs) {
     rc = launch_tridiag_extract<T>(h, n, AB, ldab, d, e);
     if (rc) return rc;
     const double rtol = sizeof(T) == 8 ? 1e-14 : 1e-9;
-    return launch_bisect(h, n, d, e, rtol, eigs, stage, stage_bytes);
+    return launch_bisect(h, n, d, e, rtol, eigs, stage, stage_bytes, nonfinite);
 }
 
 }  // namespace sev
@@ -260,11 +269,16 @@ int sev_create(sev_handle *handle, int device) {
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     h->smem_optin = (size_t)optin;
-    if (cudaMalloc(&h->d_err, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&h->d_err, sizeof(DevStatus)) != cudaSuccess) {
         delete h;
         return SEV_ERR_CUDA;
     }
-    cudaMemset(h->d_err, 0, sizeof(int));
+    const DevStatus st0{0, 0, kWaitCyclesDefault};
+    if (cudaMemcpy(h->d_err, &st0, sizeof(st0), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(h->d_err);
+        delete h;
+        return SEV_ERR_CUDA;
+    }
     if (const char *v = getenv("SEV_LEAF_ROWS")) h->leaf_rows_override = atoi(v);
     *handle = h;
     return SEV_OK;
@@ -327,6 +341,9 @@ int sev_eigvalsh(sev_handle h, int n, void *A, int lda, int b0, int prec, double
     if (b0 == 0) b0 = default_b0(n, prec);
     if (n == 1) {
         // a 1 x 1 matrix: its entry is the eigenvalue
+        const int rc = prec == SEV_FP64 ? launch_check_finite<double>(h, 1, (const double *)A, lda, nullptr)
+                                        : launch_check_finite<float>(h, 1, (const float *)A, lda, nullptr);
+        if (rc) return rc;
         if (prec == SEV_FP64) {
             SEV_CUDA(cudaMemcpyAsync(eigs, A, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
             return SEV_OK;
@@ -390,6 +407,9 @@ int sev_full_to_band(sev_handle h, int n, void *A, int lda, int b, int prec, voi
     const size_t need = prec == SEV_FP64 ? full_to_band_workspace<double>(h, n, b) : full_to_band_workspace<float>(h, n, b);
     void *ws = nullptr;
     int rc = get_workspace(h, need, &ws);
+    if (rc) return rc;
+    rc = prec == SEV_FP64 ? launch_check_finite<double>(h, n, (const double *)A, lda, nullptr)
+                          : launch_check_finite<float>(h, n, (const float *)A, lda, nullptr);
     if (rc) return rc;
     return prec == SEV_FP64 ? launch_full_to_band<double>(h, n, (double *)A, lda, b, (double *)AB, ldab, ws, need)
                             : launch_full_to_band<float>(h, n, (float *)A, lda, b, (float *)AB, ldab, ws, need);
@@ -677,6 +697,17 @@ int sev_get_error(sev_handle h) {
     if (cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SEV_ERR_CUDA;
     if (v) cudaMemset(h->d_err, 0, sizeof(int));
     return v;
+}
+
+int sev_set_wait_limit(sev_handle h, long long cycles) {
+    if (!h) return -1;
+    if (cycles < 0) return -2;
+    if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
+    const long long v = cycles == 0 ? kWaitCyclesDefault : cycles;
+    // ordered after the work already enqueued on the handle's stream
+    SEV_CUDA(cudaStreamSynchronize(h->stream));
+    SEV_CUDA(cudaMemcpy((char *)h->d_err + offsetof(DevStatus, wait_cycles), &v, sizeof(v), cudaMemcpyHostToDevice));
+    return SEV_OK;
 }
 
 const char *sev_status_string(int code) {

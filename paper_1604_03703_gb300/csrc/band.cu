@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int 
                             s_abort = 1;
                             break;
                         }
-                        if (wait_expired(t0)) {
+                        if (wait_expired(t0, err)) {
                             latch_error(err, SEV_ERR_TIMEOUT);
                             s_abort = 1;
                             break;

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                     const int need = min(t, Jf);
                     const long long t0 = clock64();
                     while (s_avail < need && !s_abort) {
-                        if (wait_expired(t0)) {
+                        if (wait_expired(t0, err)) {
                             latch_error(err, SEV_ERR_TIMEOUT);
                             s_abort = 1;
                         }
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                                 pv = -1;
                                 break;
                             }
-                            if (wait_expired(t0)) {
+                            if (wait_expired(t0, err)) {
                                 latch_error(err, SEV_ERR_TIMEOUT);
                                 pv = -1;
                                 break;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                 if (lane == 0) {
                     const long long t0 = clock64();
                     while (s_wblo < hi - wcap && !s_abort) {
-                        if (wait_expired(t0)) {
+                        if (wait_expired(t0, err)) {
                             latch_error(err, SEV_ERR_TIMEOUT);
                             s_abort = 1;
                         }
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                 if (lane == 0) {
                     const long long t0 = clock64();
                     while ((ts = s_done) <= written && !s_abort) {
-                        if (wait_expired(t0)) {
+                        if (wait_expired(t0, err)) {
                             latch_error(err, SEV_ERR_TIMEOUT);
                             s_abort = 1;
                         }

@@ -156,7 +156,7 @@ __device__ bool batch_band_to_tri(const T *A, int n, int lda, unsigned char *sme
                 if (lane == 0) {
                     const long long t0 = clock64();
                     while (sval[(i - 2) % kBatchWarps] < need) {
-                        if (*(volatile int *)&s_fail || wait_expired(t0)) {
+                        if (*(volatile int *)&s_fail || wait_expired(t0, err)) {
                             ok = 0;
                             break;
                         }

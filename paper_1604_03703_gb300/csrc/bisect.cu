@@ -1,5 +1,6 @@
 // bisect.cu -- eigenvalues of the final symmetric tridiagonal by Sturm-count
-// bisection (the "compute its eigenvalues" step of Algorithm 4.3), plus the
+// bisection (the last step of Algorithm 4.3, which returns the tridiagonal's
+// eigenvalues as the result), plus the
 // small copy kernels between dense, packed-band and tridiagonal storage.
 //
 // The bisection runs on T scaled by an exact power of two 2^-s that brings
@@ -13,6 +14,8 @@
 // operation is written with an explicit round-to-nearest intrinsic so no
 // multiply-add is contracted: the result is the exact IEEE evaluation of the
 // recurrence in the order written.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace sev {
@@ -58,6 +61,29 @@ int launch_tridiag_extract(sev_ctx *h, int n, const T *AB, int ldab, double *d, 
     return SEV_OK;
 }
 
+// Non-finite scan of the lower triangle (diagonal included): CTA c takes
+// columns c, c + grid, ...; its threads read down a column (coalesced).
+template <typename T>
+__global__ void check_finite_kernel(int n, const T *__restrict__ A, int lda, int *__restrict__ flag, int *err) {
+    bool bad = false;
+    for (int j = blockIdx.x; j < n; j += gridDim.x)
+        for (int i = j + threadIdx.x; i < n; i += blockDim.x) bad |= !isfinite(A[(size_t)i + (size_t)j * lda]);
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) {
+        latch_error(err, SEV_ERR_NONFINITE);
+        if (flag) atomicExch(flag, 1);
+    }
+}
+
+template <typename T>
+int launch_check_finite(sev_ctx *h, int n, const T *A, int lda, int *flag) {
+    if (n <= 0) return SEV_OK;
+    int grid = n < h->sm_count * 8 ? n : h->sm_count * 8;
+    SEV_LAUNCH(h, K_CHECK_FINITE, check_finite_kernel<T>, grid, kThreads, 0, n, A, lda, flag, h->d_err);
+    return SEV_OK;
+}
+
+template int launch_check_finite<float>(sev_ctx *, int, const float *, int, int *);
+template int launch_check_finite<double>(sev_ctx *, int, const double *, int, int *);
 template int launch_band_from_dense<float>(sev_ctx *, int, const float *, int, int, float *, int);
 template int launch_band_from_dense<double>(sev_ctx *, int, const double *, int, int, double *, int);
 template int launch_tridiag_extract<float>(sev_ctx *, int, const float *, int, double *, double *);
@@ -66,14 +92,15 @@ template int launch_tridiag_extract<double>(sev_ctx *, int, const double *, int,
 // ----------------------------------------------------------------- bisection
 // par[0] = gl, par[1] = gu (scaled, widened Gershgorin interval), par[2] = sc
 // = 2^-s, par[3] = tnorm (scaled max |end| of the unwidened interval),
-// par[4] = 2^s, par[5] = 1 if T = 0 (a zero Gershgorin bound).  e2s[i] =
-// (e_i 2^-s)^2.
+// par[4] = 2^s, par[5] = 1 if T = 0 (a zero Gershgorin bound), par[6] = 1 if
+// the caller's skip flag was set (non-finite input: no bisection, NaN
+// eigenvalues).  e2s[i] = (e_i 2^-s)^2.
 __device__ __forceinline__ double pow2_exact(int k) {  // 2^k, -1022 <= k <= 1023
     return __longlong_as_double((long long)(1023 + k) << 52);
 }
 
 __global__ void bisect_prep_kernel(int n, const double *__restrict__ d, const double *__restrict__ e,
-                                   double *__restrict__ e2s, double *__restrict__ par) {
+                                   double *__restrict__ e2s, double *__restrict__ par, const int *skip) {
     __shared__ double red[32];
     __shared__ double s_sc;
     double lo = INFINITY, hi = -INFINITY;
@@ -101,6 +128,7 @@ __global__ void bisect_prep_kernel(int n, const double *__restrict__ d, const do
         par[3] = tnorm;
         par[4] = pow2_exact(s);
         par[5] = tnorm == 0.0 ? 1.0 : 0.0;
+        par[6] = (skip && *skip) ? 1.0 : 0.0;
         s_sc = sc;
     }
     __syncthreads();
@@ -234,7 +262,7 @@ __device__ bool bis_barrier(BisCtl *ctl, int seq, int *err) {
                 ok = 0;
                 break;
             }
-            if (wait_expired(t0)) {
+            if (wait_expired(t0, err)) {
                 latch_error(err, SEV_ERR_TIMEOUT);
                 *(volatile int *)&ctl->abort = 1;
                 ok = 0;
@@ -290,6 +318,10 @@ __global__ void __launch_bounds__(kBisThreads) bisect_rounds_kernel(int n, const
     const double atol = __dmul_rn(rtol, par[3]);
     const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const int gthreads = gridDim.x * blockDim.x;
+    if (par[6] != 0.0) {  // non-finite input (every CTA reads the same flag: no barrier is entered)
+        for (int k = gtid; k < n; k += gthreads) eigs[k] = __longlong_as_double(0x7ff8000000000000LL);
+        return;
+    }
     const int zero = par[5] != 0.0;  // T = 0: every eigenvalue is exactly 0 (lo = hi = 0, finished)
     for (int k = gtid; k < n; k += gthreads) {
         W.lo[k] = zero ? 0.0 : par[0];
@@ -429,7 +461,7 @@ size_t bisect_workspace(int n) {
 }
 
 int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rtol, double *eigs, void *ws,
-                  size_t ws_bytes) {
+                  size_t ws_bytes, const int *skip) {
     if (n <= 0) return SEV_OK;
     if (ws_bytes < bisect_workspace(n)) return SEV_ERR_WORKSPACE;
     Carver c(ws);
@@ -444,7 +476,7 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     W.leadof = c.take<int>((size_t)n);
     W.cnt = c.take<int>((size_t)(n > kBisMaxItems ? n : kBisMaxItems));
     W.ctl = c.take<BisCtl>(1);
-    SEV_LAUNCH(h, K_BISECT_PREP, bisect_prep_kernel, 1, 1024, 0, n, d, e, e2, par);
+    SEV_LAUNCH(h, K_BISECT_PREP, bisect_prep_kernel, 1, 1024, 0, n, d, e, e2, par, skip);
     if (n == 1) {
         SEV_CUDA(cudaMemcpyAsync(eigs, d, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
         return SEV_OK;
@@ -474,19 +506,31 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
 }  // namespace sev
 
 // ------------------------------------------------- allocation-free variant
-// sev_tridiag_bisect_static: the same two kernels as sev_tridiag_bisect, but
-// their scratch (the squared scaled off-diagonal, the scaling and Gershgorin
-// parameters and an unused status slot) lives in this file-scope device array instead
-// of handle workspace, so a call allocates nothing.  The array is
-// (kStaticMaxN + 8) doubles (~512 KiB) on every device that loads the
+// sev_tridiag_bisect_static runs bisect_prep_kernel (the kernel
+// sev_tridiag_bisect also starts with) and then bisect_kernel, one thread per
+// eigenvalue index.  The handle path runs the cooperative bisect_rounds_kernel
+// instead; for every index that kernel takes the same IEEE operations in the
+// same order as bisect_kernel (the shared-interval rounds only change which
+// thread evaluates a count, never its value), so both give the same bits.
+// The scratch -- the squared scaled off-diagonal, the scaling and Gershgorin
+// parameters and the status word -- lives in this file-scope device array
+// instead of handle workspace, so a call allocates nothing.  The array is
+// (kStaticMaxN + 16) doubles (~512 KiB) on every device that loads the
 // library, held until the process exits.
 namespace sev {
 constexpr int kStaticMaxN = 65536;
-static __device__ __align__(256) double g_bisect_scratch[kStaticMaxN + 8];
+constexpr int kStaticPar = kStaticMaxN + 1;     // 8 doubles of bisection parameters
+constexpr int kStaticStatus = kStaticMaxN + 9;  // status word (a DevStatus-sized slot)
+static __device__ __align__(256) double g_bisect_scratch[kStaticMaxN + 16];
 
+// The array's device address and the SM count, per device ordinal.  They are
+// looked up again by every call made outside stream capture (so a
+// cudaDeviceReset, which reloads the module at a new address, is picked up)
+// and published atomically (concurrent first calls from several host
+// threads store the same values).
 struct StaticScratch {
-    double *ptr = nullptr;
-    int sm_count = 0;
+    std::atomic<double *> ptr{nullptr};
+    std::atomic<int> sm_count{0};
 };
 static StaticScratch g_static_dev[128];
 }  // namespace sev
@@ -502,26 +546,31 @@ extern "C" int sev_tridiag_bisect_static(int n, const double *d, const double *e
     if (n == 0) return SEV_OK;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return SEV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SEV_ERR_CUDA;
     StaticScratch &S = g_static_dev[dev];
-    if (!S.ptr) {
-        // once per device, with that device current: the array's device
-        // address (the host-side name is only a stand-in for it)
+    double *ptr = S.ptr.load(std::memory_order_acquire);
+    if (cap == cudaStreamCaptureStatusNone || !ptr) {
+        // with the device current: the array's device address (in host code
+        // the array's name is only a stand-in for it)
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_bisect_scratch) != cudaSuccess) return SEV_ERR_CUDA;
         int sms = 0;
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return SEV_ERR_CUDA;
-        S.sm_count = sms;
-        S.ptr = (double *)p;
+        S.sm_count.store(sms, std::memory_order_relaxed);
+        ptr = (double *)p;
+        S.ptr.store(ptr, std::memory_order_release);
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    double *e2 = S.ptr;                     // n + 1 doubles
-    double *par = S.ptr + kStaticMaxN + 1;  // 6 doubles
-    int *status = (int *)(S.ptr + kStaticMaxN + 7);
+    const int sm_count = S.sm_count.load(std::memory_order_relaxed);
+    double *e2 = ptr;                  // n + 1 doubles
+    double *par = ptr + kStaticPar;    // 8 doubles
+    int *status = (int *)(ptr + kStaticStatus);
     if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SEV_ERR_CUDA;
-    bisect_prep_kernel<<<1, 1024, 0, st>>>(n, d, n > 1 ? e : d, e2, par);
+    bisect_prep_kernel<<<1, 1024, 0, st>>>(n, d, n > 1 ? e : d, e2, par, nullptr);
     if (cudaGetLastError() != cudaSuccess) return SEV_ERR_CUDA;
     int bs = 64;
-    while (bs > 32 && (n + bs - 1) / bs < S.sm_count) bs >>= 1;
+    while (bs > 32 && (n + bs - 1) / bs < sm_count) bs >>= 1;
     bisect_kernel<<<(n + bs - 1) / bs, bs, 0, st>>>(n, d, e2, par, rtol, 200, eigs, status);
     return cudaGetLastError() == cudaSuccess ? SEV_OK : SEV_ERR_CUDA;
 }

@@ -38,6 +38,7 @@ enum KernelId {
     K_SPLIT_BF16,
     K_SYR2K_TC,
     K_BATCH,
+    K_CHECK_FINITE,
     K_MISC,
     K_COUNT
 };
@@ -60,7 +61,7 @@ struct sev_ctx {
     size_t ws_own_bytes = 0;
     void *ws_ext = nullptr;
     size_t ws_ext_bytes = 0;
-    int *d_err = nullptr;       // device error word (first error latched)
+    int *d_err = nullptr;       // device status block (DevStatus): error word, wait limit
     void *h_stage = nullptr;    // device staging buffer for the host entry point
     size_t h_stage_bytes = 0;
     unsigned long long timing = 0;  // bit k: time kernel id k
@@ -117,10 +118,20 @@ int get_workspace(sev_ctx *h, size_t bytes, void **out);
 __device__ __forceinline__ void latch_error(int *err, int code) { atomicCAS(err, 0, code); }
 
 constexpr int kThreads = 256;
-constexpr long kSpinCap = 20000000;  // ~ a few seconds of polling with back-off
-// Time limit of every device-side wait, in SM clock cycles (~2 s at 2 GHz).
-constexpr long long kWaitCycles = 4000000000LL;
-__device__ __forceinline__ bool wait_expired(long long t0) { return clock64() - t0 > kWaitCycles; }
+// The handle's device status block: the latched error word (first error
+// wins), then the time limit of every device-side wait in SM clock cycles
+// (default ~2 s at 2 GHz; sev_set_wait_limit changes it per handle).  Kernels
+// receive a pointer to it as `int *err`.
+struct DevStatus {
+    int err;
+    int pad;
+    long long wait_cycles;
+};
+constexpr long long kWaitCyclesDefault = 4000000000LL;
+__device__ __forceinline__ long long wait_cap(const int *err) {
+    return reinterpret_cast<const DevStatus *>(err)->wait_cycles;
+}
+__device__ __forceinline__ bool wait_expired(long long t0, const int *err) { return clock64() - t0 > wait_cap(err); }
 
 // ------------------------------------------------------ reductions (CTA-wide)
 __device__ __forceinline__ double warp_sum(double v) {
@@ -758,8 +769,15 @@ template <typename T>
 int launch_band_from_dense(sev_ctx *h, int n, const T *A, int lda, int b, T *AB, int ldab);
 template <typename T>
 int launch_tridiag_extract(sev_ctx *h, int n, const T *AB, int ldab, double *d, double *e);
+// skip (device, may be null): when *skip != 0 at run time the bisection does
+// no work and writes NaN eigenvalues (set by launch_check_finite).
 int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rtol, double *eigs, void *ws,
-                  size_t ws_bytes);
+                  size_t ws_bytes, const int *skip = nullptr);
+// Scans the lower triangle of A (n x n, lda); if it holds a NaN or an Inf,
+// latches SEV_ERR_NONFINITE and sets *flag (device, may be null; the caller
+// zeroes it first).
+template <typename T>
+int launch_check_finite(sev_ctx *h, int n, const T *A, int lda, int *flag);
 size_t bisect_workspace(int n);
 
 // band.cu

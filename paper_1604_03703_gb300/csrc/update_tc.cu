@@ -49,12 +49,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
         : "memory");
     return ok != 0;
 }
-// Capped wait on an mbarrier phase; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase) {
+// Wait on an mbarrier phase for at most `cap` SM cycles; false on timeout.
+__device__ __forceinline__ bool mbar_wait_for(uint64_t *bar, uint32_t phase, long long cap) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, phase))
-        if (wait_expired(t0)) return false;
+        if (clock64() - t0 > cap) return false;
     return true;
+}
+// The same with the handle's wait limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t phase, const int *err) {
+    return mbar_wait_for(bar, phase, wait_cap(err));
 }
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(128, 1)
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages], done;
     __shared__ uint32_t tmem_base;
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_issued, s_waited;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // lower tile (I, J), I >= J, from the linear block index
@@ -187,6 +191,8 @@ __global__ void __launch_bounds__(128, 1)
         mbar_init(&done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
+        s_issued = 0;
+        s_waited = 0;
     }
     if (warp == 0) {
         tmem_alloc(&tmem_base, 128);
@@ -199,9 +205,10 @@ __global__ void __launch_bounds__(128, 1)
 
     if (warp == 0 && lane == 0) {
         // TMA producer
+        int issued = 0;
         for (int ks = 0; ks < ksteps; ++ks) {
             const int s = ks % kTcStages, round = ks / kTcStages;
-            if (ks >= kTcStages && !mbar_wait(&empty[s], (round - 1) & 1)) {
+            if (ks >= kTcStages && !mbar_wait(&empty[s], (round - 1) & 1, err)) {
                 s_fail = 1;
                 break;
             }
@@ -209,13 +216,16 @@ __global__ void __launch_bounds__(128, 1)
             mbar_expect_tx(&full[s], kTcStageBytes);
             tma_load_2d(st, &mapP, ks * 64, I * 128, &full[s]);
             tma_load_2d(st + kTcStageBytes / 2, &mapQ, ks * 64, J * 128, &full[s]);
+            ++issued;
         }
+        s_issued = issued;
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         bool ok = true;
+        int waited = 0;
         for (int ks = 0; ks < ksteps; ++ks) {
             const int s = ks % kTcStages, round = ks / kTcStages;
-            if (!mbar_wait(&full[s], round & 1)) {
+            if (!mbar_wait(&full[s], round & 1, err)) {
                 ok = false;
                 s_fail = 1;
                 break;
@@ -227,13 +237,15 @@ __global__ void __launch_bounds__(128, 1)
             for (int kk = 0; kk < 4; ++kk)  // K = 16 per instruction: +32 bytes = +2 in the address field
                 umma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, kIdescBF16_128x128, (ks | kk) != 0);
             umma_commit(&empty[s]);
+            ++waited;
         }
+        s_waited = waited;
         if (ok) umma_commit(&done);
     }
     __syncwarp();
     // epilogue: every thread waits for the accumulator
     // warp-uniform decision: tcgen05.ld is .sync.aligned
-    const bool have = __all_sync(0xffffffffu, mbar_wait(&done, 0) ? 1 : 0) && !s_fail;
+    const bool have = __all_sync(0xffffffffu, mbar_wait(&done, 0, err) ? 1 : 0) && !s_fail;
     tc_fence_after();
     if (have) {
         const int row = I * 128 + warp * 32 + lane;
@@ -263,6 +275,19 @@ __global__ void __launch_bounds__(128, 1)
         }
     } else if (threadIdx.x == 0) {
         latch_error(err, SEV_ERR_TIMEOUT);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s_fail && threadIdx.x == 0) {
+        // a wait ran out: before the CTA frees its TMEM and leaves, let the
+        // copies it issued land and the MMAs it committed finish (each with
+        // the default limit, whatever the handle's limit is)
+        for (int ks = s_waited; ks < s_issued; ++ks)
+            mbar_wait_for(&full[ks % kTcStages], (ks / kTcStages) & 1, kWaitCyclesDefault);
+        if (s_waited > 0) {
+            const int last = s_waited - 1;
+            mbar_wait_for(&empty[last % kTcStages], (last / kTcStages) & 1, kWaitCyclesDefault);
+        }
     }
     tc_fence_before();
     __syncthreads();

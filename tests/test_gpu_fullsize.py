@@ -54,7 +54,7 @@ def clean_shifts(count_fn, xs, delta, want=4):
 # ----------------------------------------------------------------- bisection
 @pytest.mark.parametrize("rtol", [1e-9, 1e-14])
 @pytest.mark.parametrize("kind", ["random", "clustered"])
-def test_bisect_n16384_sampled_bitwise(H, torch_cuda, orc, rtol, kind):
+def test_bisect_n16384_sampled_vs_oracles(H, torch_cuda, orc, rtol, kind):
     torch = torch_cuda
     n = 16384
     if kind == "random":
@@ -67,6 +67,10 @@ def test_bisect_n16384_sampled_bitwise(H, torch_cuda, orc, rtol, kind):
     ks = np.unique(np.concatenate([np.arange(0, 8), np.arange(n - 8, n), np.linspace(0, n - 1, 48).astype(int)]))
     for k in ks:
         assert got[k] == orc.bisect_range(d, e, int(k), int(k) + 1, rtol)[0], k
+    # the textbook LDL^T bisection (independent count, unscaled interval) at the same indices
+    ref = orc.bisect_ldlt(d, e, rtol, ks)
+    tn = orc.gershgorin(d, e)[2]
+    assert np.all(np.abs(got[ks] - ref) <= np.maximum(rtol * np.abs(ref), rtol * tn) + 8 * EPS64 * tn)
 
 
 # --------------------------------------------------------------- band stages

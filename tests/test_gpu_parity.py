@@ -51,8 +51,44 @@ def band_dense(AB_t):
 
 
 # ----------------------------------------------------------------- bisection
+def ldlt_tolerance(orc, d, e, rtol, ref):
+    """|lambda_gpu - lambda_ldlt| bound: each side stops on an interval of
+    width <= max(rtol |lambda|, rtol ||T||_G) around the transition of its own
+    Sturm count, and each count is exact for a matrix within a few units of
+    roundoff of T (backward stability of the Sturm sequence), so the two
+    transitions differ by at most 8 u ||T||_G."""
+    tn = orc.gershgorin(d, e)[2] if len(d) > 1 else abs(d[0])
+    return np.maximum(rtol * np.abs(ref), rtol * tn) + 8 * EPS64 * tn
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (3, 2), (37, 3), (1000, 4), (1777, 6)])
+def test_bisect_vs_textbook_ldlt_oracle(H, torch_cuda, orc, n, seed):
+    """The GPU bisection (minors count on the rescaled matrix) against the
+    plain LDL^T-pivot-count bisection with the pivmin guard, from the
+    unscaled Gershgorin interval: the textbook definition of the step."""
+    torch = torch_cuda
+    d, e = I.random_tridiagonal(n, 100 + seed)
+    for rtol in (1e-14, 1e-9):
+        got = H.tridiag_bisect(dev(torch, d), dev(torch, e), rtol).cpu().numpy()
+        H.raise_device_error()
+        ref = orc.bisect_ldlt(d, e, rtol)
+        assert np.all(np.abs(got - ref) <= ldlt_tolerance(orc, d, e, rtol, ref))
+
+
+def test_bisect_vs_textbook_ldlt_toeplitz_clusters_zeros(H, torch_cuda, orc):
+    torch = torch_cuda
+    cases = [I.toeplitz(777, 0.5, -1.25)[:2], (np.repeat(np.array([-1.0, 0.0, 2.0]), 50), np.where(np.arange(149) % 7 == 0, 1e-12, 0.0))]
+    for d, e in cases:
+        got = H.tridiag_bisect(dev(torch, d), dev(torch, e), 1e-14).cpu().numpy()
+        ref = orc.bisect_ldlt(d, e, 1e-14)
+        assert np.all(np.abs(got - ref) <= ldlt_tolerance(orc, d, e, 1e-14, ref))
+
+
 @pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (3, 2), (37, 3), (1000, 4), (4099, 5)])
-def test_bisect_bitwise_vs_oracle(H, torch_cuda, orc, n, seed):
+def test_bisect_bitwise_vs_minors_restatement(H, torch_cuda, orc, n, seed):
+    """Bitwise agreement with the oracle's restatement of the kernel's
+    arithmetic (the minors count on the exactly rescaled matrix, the same
+    IEEE operations in the same order); the textbook tests above pin it."""
     torch = torch_cuda
     d, e = I.random_tridiagonal(n, 100 + seed)
     got = H.tridiag_bisect(dev(torch, d), dev(torch, e), 1e-14).cpu().numpy()
@@ -183,6 +219,34 @@ def test_eigvalsh_qdq512_fp64(H, torch_cuda, orc):
     assert np.abs(got - D).max() <= 1e-11 * norm
 
 
+def test_qdq512_halving_schedule_through_stage_calls(H, torch_cuda, orc):
+    """The n = 512 workload along the paper's halving schedule, b0 = 32 ->
+    16 -> 8 -> 4 -> 2 -> 1 (Algorithm 4.3 with k = 2), through the stage
+    entry points: every intermediate band against the oracle's stage
+    (entrywise), the eigenvalues against the oracle's staged pipeline and the
+    prescribed spectrum D."""
+    torch = torch_cuda
+    A, D = I.workload_qdq512()
+    n, b0 = 512, 32
+    sched = orc.band_schedule(b0)
+    assert sched == [32, 16, 8, 4, 2, 1]
+    AB = H.full_to_band(dev(torch, A, torch.float64), b0)
+    ref = orc.full_to_band(A, b0)
+    scale = np.linalg.norm(A)
+    for b, hh in zip(sched[:-1], sched[1:]):
+        H.band_to_band(AB, b, hh)
+        H.raise_device_error()
+        ref = orc.band_to_band(ref, b, hh)
+        np.testing.assert_allclose(np.tril(band_dense(AB)), np.tril(ref), atol=20 * n * EPS64 * scale, rtol=0)
+    d_t, e_t = H.band_tridiag(AB)
+    got = H.tridiag_bisect(d_t, e_t, 1e-14).cpu().numpy()
+    H.raise_device_error()
+    staged = orc.eigvalsh_via_stages(A, b0, 1e-14)
+    norm = np.abs(D).max()
+    assert np.abs(got - staged).max() <= 1e-11 * norm
+    assert np.abs(got - D).max() <= 1e-11 * norm
+
+
 def test_eigvalsh_qdq512_mixed(H, torch_cuda, orc):
     torch = torch_cuda
     A, D = I.workload_qdq512()
@@ -282,3 +346,67 @@ def test_pairfloat_house_scalars_equal_fp64_rounded(H, torch_cuda):
     assert rc == 0
     torch.cuda.synchronize()
     assert torch.equal(o1, o2)
+
+
+# ---------------------------------------------------- failure detection
+@pytest.mark.parametrize("dtype_name,bad", [("float64", "nan"), ("float32", "inf"), ("float32", "nan")])
+def test_nonfinite_input_latched_then_handle_still_solves(torch_cuda, orc, dtype_name, bad):
+    """A NaN or Inf placed on the host in the lower triangle latches
+    SEV_ERR_NONFINITE; the eigenvalues come back NaN; the same handle then
+    solves a clean matrix to the usual tolerance."""
+    torch = torch_cuda
+    from paper_1604_03703_gb300 import api
+    from paper_1604_03703_gb300 import build as B
+
+    B.build()
+    h = api.Handle(0)
+    dtype = getattr(torch, dtype_name)
+    n = 300
+    A = I.semicircle(n, 9300)
+    Abad = A.copy()
+    Abad[200, 17] = np.nan if bad == "nan" else np.inf
+    got = h.eigvalsh(dev(torch, Abad, dtype), 16).cpu().numpy()
+    assert h.get_error() == 1  # SEV_ERR_NONFINITE
+    assert np.all(np.isnan(got))
+    AB = h.full_to_band(dev(torch, Abad, dtype), 16)
+    assert h.get_error() == 1
+    got = h.eigvalsh(dev(torch, A, dtype), 16).cpu().numpy()
+    h.raise_device_error()
+    ref = orc.eigvalsh(A, 1e-14)
+    tol = 1e-11 if dtype_name == "float64" else 1e-4
+    assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+    h.close()
+
+
+def test_wait_limit_runs_out_then_handle_still_solves(torch_cuda, orc):
+    """With the handle's wait limit cut to 2000 SM cycles (~1 us), a b -> h
+    band stage, whose sweep i must wait for sweep i-1's third chase, hits the
+    limit: SEV_ERR_TIMEOUT is latched and every CTA returns.  With the default
+    limit restored, the same handle reduces a band and solves a matrix
+    correctly."""
+    torch = torch_cuda
+    from paper_1604_03703_gb300 import api
+    from paper_1604_03703_gb300 import build as B
+
+    B.build()
+    h = api.Handle(0)
+    n, b, hh = 2000, 64, 32
+    A = I.random_band(n, b, 9400)
+    AB = to_band_tensor(torch, A, 2 * b, torch.float64)
+    h.set_wait_limit(2000)
+    try:
+        h.band_to_band(AB, b, hh)
+        assert h.get_error() == 3  # SEV_ERR_TIMEOUT
+    finally:
+        h.set_wait_limit(0)
+    AB = to_band_tensor(torch, A, 2 * b, torch.float64)
+    h.band_to_band(AB, b, hh)
+    h.raise_device_error()
+    ref = orc.band_to_band(A, b, hh)
+    np.testing.assert_allclose(np.tril(band_dense(AB)), np.tril(ref), atol=20 * n * EPS64 * np.linalg.norm(A), rtol=0)
+    M = I.semicircle(257, 9401)
+    got = h.eigvalsh(dev(torch, M, torch.float64), 32).cpu().numpy()
+    h.raise_device_error()
+    ref = orc.eigvalsh(M, 1e-14)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+    h.close()

@@ -40,23 +40,57 @@ def _static(torch, lib, d_t, e_t, rtol, out_t):
                                          float(rtol), ctypes.c_void_p(out_t.data_ptr()), ctypes.c_void_p(stream))
 
 
-def test_static_bisect_matches_handle_two_calls(env):
+def _cases():
+    d_cl = np.repeat(np.array([-1.0, 0.0, 2.0]), 40)
+    e_cl = np.where(np.arange(119) % 7 == 0, 1e-12, 0.0)
+    return [
+        ("random n=3001", *I.random_tridiagonal(3001, 41), 1e-14),
+        ("toeplitz n=5000", *I.toeplitz(5000, 0.25, -1.5)[:2], 1e-9),
+        ("n=1", np.array([0.75]), np.zeros(0), 1e-14),
+        ("n=2", np.array([1.0, 3.0]), np.array([2.0]), 1e-14),
+        ("T=0", np.zeros(64), np.zeros(63), 1e-14),
+        ("clusters", d_cl, e_cl, 1e-14),
+        # the largest order: the parameters and status word sit right after
+        # the n + 1 squared off-diagonals at the end of the fixed array
+        ("random n=65536", *I.random_tridiagonal(65536, 42), 1e-9),
+    ]
+
+
+@pytest.mark.parametrize("case", range(7))
+def test_static_bisect_matches_handle_two_calls(env, case):
+    """Two calls in a row on the same fixed array: each equals the handle's
+    sev_tridiag_bisect bit for bit."""
     torch, lib, h = env
-    cases = [I.random_tridiagonal(3001, 41), I.toeplitz(5000, 0.25, -1.5)[:2]]
-    for rtol, (d, e) in zip([1e-14, 1e-9], cases):
-        d_t = torch.tensor(d, dtype=torch.float64, device="cuda")
-        e_t = torch.tensor(e, dtype=torch.float64, device="cuda")
-        out = torch.empty_like(d_t)
-        assert _static(torch, lib, d_t, e_t, rtol, out) == 0
-        ref = h.tridiag_bisect(d_t, e_t, rtol)
+    name, d, e, rtol = _cases()[case]
+    d_t = torch.tensor(d, dtype=torch.float64, device="cuda")
+    e_t = torch.tensor(e if e.size else np.zeros(1), dtype=torch.float64, device="cuda")
+    ref = h.tridiag_bisect(d_t, e_t[: max(d.size - 1, 0)], rtol).cpu().numpy()
+    for call in range(2):
+        out = torch.full_like(d_t, np.nan)
+        assert _static(torch, lib, d_t, e_t, rtol, out) == 0, (name, call)
         torch.cuda.synchronize()
-        np.testing.assert_array_equal(out.cpu().numpy(), ref.cpu().numpy())
+        np.testing.assert_array_equal(out.cpu().numpy(), ref, err_msg="%s call %d" % (name, call))
 
 
-def test_static_bisect_rejects_oversize_and_bad_rtol(env):
+def test_static_bisect_argument_checks(env):
+    """Every argument error is refused on the host before anything is
+    launched; n = 0 is a no-op and n = 65536, the fixed maximum, is accepted."""
     torch, lib, _ = env
-    d_t = torch.zeros(4, dtype=torch.float64, device="cuda")
+    d_t = torch.zeros(65536, dtype=torch.float64, device="cuda")
+    out = torch.full_like(d_t, np.nan)
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     p = ctypes.c_void_p(d_t.data_ptr())
-    assert lib.sev_tridiag_bisect_static(65537, p, p, 1e-14, p, stream) == -1
-    assert lib.sev_tridiag_bisect_static(4, p, p, 1e-20, p, stream) == -4
+    o = ctypes.c_void_p(out.data_ptr())
+    null = ctypes.c_void_p(0)
+    assert lib.sev_tridiag_bisect_static(65537, p, p, 1e-14, o, stream) == -1
+    assert lib.sev_tridiag_bisect_static(-1, p, p, 1e-14, o, stream) == -1
+    assert lib.sev_tridiag_bisect_static(4, null, p, 1e-14, o, stream) == -2
+    assert lib.sev_tridiag_bisect_static(4, p, null, 1e-14, o, stream) == -3
+    assert lib.sev_tridiag_bisect_static(4, p, p, 1e-20, o, stream) == -4
+    assert lib.sev_tridiag_bisect_static(4, p, p, 1.0, o, stream) == -4
+    assert lib.sev_tridiag_bisect_static(4, p, p, 1e-14, null, stream) == -5
+    assert lib.sev_tridiag_bisect_static(0, null, null, 1e-14, null, stream) == 0
+    assert lib.sev_tridiag_bisect_static(1, p, null, 1e-14, o, stream) == 0  # n = 1 reads no e
+    assert lib.sev_tridiag_bisect_static(65536, p, p, 1e-14, o, stream) == 0  # T = 0 at the maximum order
+    torch.cuda.synchronize()
+    assert np.all(out.cpu().numpy() == 0.0)
