@@ -806,7 +806,24 @@ void batch_pack_mat(void *dst, void *A, double *eigs, int n, int lda);
 template <typename T>
 int launch_batch_fill(sev_ctx *h, int count, const void *mats, unsigned long long seed);
 
-// panel.cu + update.cu
+// panel.cu + panel_reg.cu + update.cu
+// Buffers of the register-resident panel factorisation (panel_reg.cu).
+template <typename T>
+struct RegPanelBufs {
+    T *Yleaf, *Ynode, *tau, *Rbuf, *Zbuf, *Q, *Winv;
+    int *nref;
+};
+template <typename T>
+int reg_panel_supported(int b);
+template <typename T>
+int reg_panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, const RegPanelBufs<T> &B);
+// T and the band block of a one-leaf panel (U explicit, tau, R from the leaf QR).
+template <typename T>
+int panel_finish_single_leaf(sev_ctx *h, int N, int b, const T *U, const T *tau, const int *nref, const T *R, T *Tm,
+                             T *P, int lda);
+// U[b:N] = Q[b:N] W1^{-1}; zeroes the panel below its top b rows.
+template <typename T>
+int panel_form_u2(sev_ctx *h, int N, int b, const T *Q, const T *Winv, T *U, T *P, int lda);
 template <typename T>
 int launch_full_to_band(sev_ctx *h, int n, T *A, int lda, int b, T *AB, int ldab, void *ws, size_t ws_bytes);
 template <typename T>

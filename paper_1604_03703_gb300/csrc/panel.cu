@@ -466,18 +466,61 @@ static void carve_panel(Carver &c, PanelBuffers<T> &B, int n, int b, int r_leaf,
     B.nref = c.take<int>((size_t)nodes);
 }
 
+// Register path: leaves of at least b rows, binary tree.
+template <typename T>
+static void carve_reg_panel(Carver &c, RegPanelBufs<T> &B, int n, int b) {
+    const int Lmax = n / b + 1;
+    const int nodes = 2 * Lmax + 64;
+    B.Yleaf = c.take<T>((size_t)n * b);
+    B.Ynode = c.take<T>((size_t)(Lmax + 64) * 2 * b * b);
+    B.tau = c.take<T>((size_t)nodes * b);
+    B.Rbuf = c.take<T>((size_t)nodes * b * b);
+    B.Zbuf = c.take<T>((size_t)nodes * b * b);
+    B.Q = c.take<T>((size_t)n * b);
+    B.Winv = c.take<T>((size_t)b * b);
+    B.nref = c.take<int>((size_t)nodes);
+}
+
 template <typename T>
 size_t panel_workspace(sev_ctx *h, int n, int b) {
     Carver c(nullptr);
     PanelBuffers<T> B;
     carve_panel<T>(c, B, n, b, pick_r_leaf<T>(b, (size_t)h->smem_optin - 1024), 2);
-    return c.bytes();
+    Carver c2(nullptr);
+    RegPanelBufs<T> B2;
+    carve_reg_panel<T>(c2, B2, n, b);
+    return c.bytes() > c2.bytes() ? c.bytes() : c2.bytes();
+}
+
+template <typename T>
+int panel_finish_single_leaf(sev_ctx *h, int N, int b, const T *U, const T *tau, const int *nref, const T *R, T *Tm,
+                             T *P, int lda) {
+    const size_t s_fin = sizeof(T) * 2 * (size_t)(b + 1) * b;
+    SEV_CUDA(cudaFuncSetAttribute(single_leaf_finish_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)s_fin));
+    SEV_LAUNCH(h, K_RECON_LU, single_leaf_finish_kernel<T>, 1, kThreads, s_fin, N, b, U, N, tau, nref, R, Tm, P, lda);
+    return SEV_OK;
+}
+
+template <typename T>
+int panel_form_u2(sev_ctx *h, int N, int b, const T *Q, const T *Winv, T *U, T *P, int lda) {
+    const size_t s_u2 = sizeof(T) * (size_t)(b + 1) * b;
+    SEV_CUDA(cudaFuncSetAttribute(recon_u2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_u2));
+    const int g2 = (N - b + 63) / 64;
+    if (g2 > 0) SEV_LAUNCH(h, K_RECON_U2, recon_u2_kernel<T>, g2, kThreads, s_u2, N, b, Q, N, Winv, U, N, P, lda);
+    return SEV_OK;
 }
 
 // Factorise the N x b panel P (lda) and produce U (N x b, ldu = N), T (b x b)
 // and the band block (written over the panel in A).
 template <typename T>
 int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws) {
+    if (reg_panel_supported<T>(b)) {
+        Carver c(ws);
+        RegPanelBufs<T> B;
+        carve_reg_panel<T>(c, B, N, b);
+        return reg_panel_factor<T>(h, N, b, P, lda, U, Tm, B);
+    }
     const size_t budget = (size_t)h->smem_optin - 1024;
     int r_leaf = pick_r_leaf<T>(b, budget);
     if (h->leaf_rows_override > 0) {
@@ -554,6 +597,12 @@ int panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, void *ws)
 template int panel_factor<float>(sev_ctx *, int, int, float *, int, float *, float *, void *);
 template int panel_factor<double>(sev_ctx *, int, int, double *, int, double *, double *, void *);
 template size_t panel_workspace<float>(sev_ctx *, int, int);
+template int panel_finish_single_leaf<float>(sev_ctx *, int, int, const float *, const float *, const int *,
+                                             const float *, float *, float *, int);
+template int panel_finish_single_leaf<double>(sev_ctx *, int, int, const double *, const double *, const int *,
+                                              const double *, double *, double *, int);
+template int panel_form_u2<float>(sev_ctx *, int, int, const float *, const float *, float *, float *, int);
+template int panel_form_u2<double>(sev_ctx *, int, int, const double *, const double *, double *, double *, int);
 template size_t panel_workspace<double>(sev_ctx *, int, int);
 
 }  // namespace sev
