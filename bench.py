@@ -168,8 +168,11 @@ def kernel_model(name, n, b0, elem):
     band stages b -> h (k = b/h): each of the n/h sweeps reads and writes the
     2b stored diagonals of the columns it passes, ~2 s 2b (n - ih) bytes, so
     2 s k n^2 bytes per stage; the b -> 1 stage is k = b.
-    tree-QR nodes: 2(2b)b^2 - (2/3)b^3 flops per stacked-triangle QR.
-    bisection: n eigenvalues x iterations x n Sturm steps (one FP64 divide each).
+    tree-QR nodes: 2(2b)b^2 - (2/3)b^3 flops per stacked-triangle QR (the
+    dense count; the kernel skips the structural zeros); leaves of at most
+    256 rows, so ceil(N/256) - 1 nodes per panel.
+    bisection: n eigenvalues x iterations x n Sturm steps (the per-eigenvalue
+    definition; each step is three FP64 instructions, division-free).
     """
     Ns = panel_sizes(n, b0)
     sched = schedule(b0, elem)
@@ -190,8 +193,7 @@ def kernel_model(name, n, b0, elem):
             tot += 2.0 * elem * (b // h) * float(n) ** 2
         return tot, "byte", "hbm"
     if name == "tsqr_node_qr":
-        r_leaf = 128 if b0 >= 64 else 256
-        nodes = sum(max(N // r_leaf - 1, 0) for N in Ns)
+        nodes = sum(max(-(-N // 256) - 1, 0) for N in Ns)
         return nodes * (4.0 * b0 ** 3 - 2.0 * b0 ** 3 / 3.0), "flop", "alu"
     if name == "bisect":
         rtol = 1e-9 if elem == 4 else 1e-14
@@ -200,15 +202,10 @@ def kernel_model(name, n, b0, elem):
     return None, None, None
 
 
-# DRAM bytes (dram__bytes_read + dram__bytes_write) per step of the bench's
-# dominant kernel, from the ncu capture summarised under profiles/.
-MEASURED_TRAFFIC = {
-    "band_chase": {
-        "bytes_per_step": 2 * 4 * 4.55e6,
-        "note": "profiles/band_chase_n4096_b128to32.md: 4.55 MB per 128->32 launch at n=4096, scaled by n "
-                "(the band is L2-resident and moves through DRAM about once) to n=16384, two launches per step",
-    },
-}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per step of a
+# kernel, taken by ncu at this benchmark's configuration (n = 16384, b0 = 128)
+# for the kernel as it is built now; a kernel absent here reports null.
+MEASURED_TRAFFIC = {}
 
 
 def roofline(name, amount, unit, bound, ms_per_step, peaks, clocks, elem):
@@ -235,24 +232,37 @@ def roofline(name, amount, unit, bound, ms_per_step, peaks, clocks, elem):
         return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_note": "of measured"}
     if unit == "sturm_step":
-        # one IEEE FP64 division per step; 59.66 G div/s measured on this GB300 at ~1995 MHz
-        peak = 59.66 * mhz / 1995.0
+        # three FP64 instructions per (division-free) Sturm step; the FP64 pipe
+        # issues 2 instructions per SM per clock (152 SMs)
+        peak = 152 * 2 * mhz * 1e6 / 3.0 / 1e9
         ach = amount / sec / 1e9
         return {"bound": "alu", "achieved": ach, "peak": peak, "unit": "Gstep/s", "frac": ach / peak,
-                "peak_note": "FP64 divide throughput (microbenchmark), clock-scaled"}
+                "peak_note": "unit counts x median SM clock: 2 FP64 instructions per SM per clock, 3 per step"}
     return None
 
 
 # ---------------------------------------------------------------- oracle leg
-def oracle_sample(A64_host, n, rtol, seconds, steps_cap=None):
+def host_cores():
+    """Cores this process may run on (read at run time)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(A64_host, n, rtol, seconds, steps_cap=None, omp=False):
     """Time the CPU oracle on a bounded sample of the workload and
     extrapolate: the first m Householder steps of the tridiagonalisation of
-    A (step j costs ~(n-1-j)^2) and k of the n bisections (equal cost each)."""
+    A (step j costs ~(n-1-j)^2) and k of the n bisections (equal cost each).
+    omp: the oracle's OpenMP build on every core (same results; None if the
+    compiler has no OpenMP runtime)."""
     import numpy as np
 
     import oracle
 
     oracle.build()
+    if omp and oracle.load_omp() is None:
+        return None
     budget_tri = 0.8 * seconds
     # per-step estimate from one step
     M = np.asfortranarray(A64_host.T)  # symmetric: the transpose is the same matrix, F-ordered view
@@ -260,14 +270,14 @@ def oracle_sample(A64_host, n, rtol, seconds, steps_cap=None):
     d = np.zeros(n)
     e = np.zeros(n)
     t0 = time.perf_counter()
-    oracle.tridiagonalize_inplace(M, d, e, 1)
+    oracle.tridiagonalize_inplace(M, d, e, 1, omp=omp)
     t1 = time.perf_counter() - t0
     m = max(1, min(n - 2, int(budget_tri / max(t1, 1e-6))))
     if steps_cap:
         m = min(m, steps_cap)
     M = np.array(np.asfortranarray(A64_host.T), order="F", copy=True)
     t0 = time.perf_counter()
-    oracle.tridiagonalize_inplace(M, d, e, m)
+    oracle.tridiagonalize_inplace(M, d, e, m, omp=omp)
     t_m = time.perf_counter() - t0
     del M
     w = (np.arange(n - 1, 1, -1, dtype=np.float64)) ** 2  # (n-1-j)^2, j = 0..n-3
@@ -276,15 +286,16 @@ def oracle_sample(A64_host, n, rtol, seconds, steps_cap=None):
     dd, ee = rng.standard_normal(n), rng.standard_normal(n - 1)
     k = 8
     t0 = time.perf_counter()
-    oracle.bisect_range(dd, ee, 0, k, rtol)
+    oracle.bisect_range(dd, ee, 0, k, rtol, omp=omp)
     tk = time.perf_counter() - t0
     k = max(8, min(n, int(0.2 * seconds / max(tk / 8, 1e-9))))
     t0 = time.perf_counter()
-    oracle.bisect_range(dd, ee, n // 2 - k // 2, n // 2 - k // 2 + k, rtol)
+    oracle.bisect_range(dd, ee, n // 2 - k // 2, n // 2 - k // 2 + k, rtol, omp=omp)
     t_k = time.perf_counter() - t0
     t_bis = t_k * n / k
     total = t_tri + t_bis
     return {
+        "cores": host_cores() if omp else 1,
         "seconds_extrapolated": total,
         "value": nominal_flops(n) / total / 1e12,
         "sample": "first %d of %d Householder steps of the oracle tridiagonalisation of the workload matrix "
@@ -306,11 +317,11 @@ def gen_workload(n, device):
 
 
 def time_plan(plan, work, orig, reps=3):
-    """Device time of plan.run() (CUDA events), best of reps; the inputs are
-    restored before every run, outside the events."""
+    """Device time of plan.run() (CUDA events), median of reps; the inputs
+    are restored before every run, outside the events."""
     import torch
 
-    best = None
+    times = []
     for _ in range(reps):
         for w, o in zip(work, orig):
             w.copy_(o)
@@ -320,9 +331,39 @@ def time_plan(plan, work, orig, reps=3):
         plan.run()
         e1.record()
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        best = ms if best is None else min(best, ms)
-    return best
+        times.append(e0.elapsed_time(e1))
+    return statistics.median(times)
+
+
+def time_plan_graph(plan, work, orig, reps=20):
+    """The plan captured once in a CUDA graph, then replayed reps times: the
+    median device time of one replay (CUDA events on the replay stream); the
+    inputs are restored before every replay, outside the events."""
+    import torch
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside capture
+        plan.run()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.run()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(reps):
+        for w, o in zip(work, orig):
+            w.copy_(o)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    del g
+    return statistics.median(times)
 
 
 def max_over_ranks(ms, world, device):
@@ -362,10 +403,11 @@ def bench_batched(h, device, args, rank=0, world=1):
         work = [t.clone() for t in orig]
         outs = [torch.empty(t.shape[0], dtype=torch.float64, device=device) for t in orig]
         plan = h.batch_plan(work, outs, b)
-        ms = max_over_ranks(time_plan(plan, work, orig), world, device)
+        ms = max_over_ranks(time_plan_graph(plan, work, orig, 20), world, device)
         h.raise_device_error("batched " + name)
         plan.close()
-        small[name] = {"ms": ms, "mats_per_s": 4096 / (ms / 1e3), "b": b, "launches": 1}
+        small[name] = {"ms": ms, "mats_per_s": 4096 / (ms / 1e3), "b": b, "launches": 1,
+                       "timing": "median of 20 replays of the plan captured in a CUDA graph"}
         del orig, work, outs
         torch.cuda.empty_cache()
     small["mixed_speedup"] = small["fp64"]["ms"] / small["mixed"]["ms"]
@@ -578,8 +620,13 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1:
-        cpu = oracle_sample(A_host64, n, 1e-9, args.cpu_seconds)
-        cpu = {"value": cpu["value"], "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": cpu["sample"]}
+        one = oracle_sample(A_host64, n, 1e-9, args.cpu_seconds / 2)
+        allc = oracle_sample(A_host64, n, 1e-9, args.cpu_seconds / 2, omp=True)
+        cpu = {"value": one["value"], "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": one["sample"]}
+        if allc is not None:
+            cpu["all_cores"] = {"value": allc["value"], "unit": "TFLOP/s", "cores": allc["cores"], "kind": "oracle",
+                                "sample": allc["sample"] + " (OpenMP build: same results, independent loops on "
+                                                           "every core)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,

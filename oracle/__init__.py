@@ -42,6 +42,45 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False):
+    """The same oracle.c compiled with OpenMP (independent loops on all
+    cores, same arithmetic per output) for the all-cores CPU baseline;
+    None if the compiler has no OpenMP runtime."""
+    if not force and os.path.exists(_LIB_OMP) and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC):
+        return _LIB_OMP
+    tmp = _LIB_OMP + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.check_call(cmd, stderr=subprocess.DEVNULL)
+    except (subprocess.CalledProcessError, OSError):
+        return None
+    os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def load_omp():
+    """Handle of the OpenMP build (orc_tridiagonalize, orc_bisect_range), or None."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            path = build_omp()
+            if path is None:
+                return None
+            lib = ctypes.CDLL(path)
+            i, d = ctypes.c_int, ctypes.c_double
+            lib.orc_tridiagonalize.restype = None
+            lib.orc_tridiagonalize.argtypes = [i, _dp, i, _dp, _dp, i]
+            lib.orc_bisect_range.restype = i
+            lib.orc_bisect_range.argtypes = [i, _dp, _dp, d, i, i, i, _dp]
+            _lib_omp = lib
+    return _lib_omp
+
+
 def _load():
     global _lib
     with _lock:
@@ -120,10 +159,12 @@ def tridiagonalize(A, nsteps: int = -1):
     return d[:n], e[: max(n - 1, 0)]
 
 
-def tridiagonalize_inplace(M: np.ndarray, d: np.ndarray, e: np.ndarray, nsteps: int) -> None:
-    """In-place form used to time a bounded sample of the reduction."""
+def tridiagonalize_inplace(M: np.ndarray, d: np.ndarray, e: np.ndarray, nsteps: int, omp: bool = False) -> None:
+    """In-place form used to time a bounded sample of the reduction (omp:
+    the OpenMP build, same results)."""
     assert M.flags.f_contiguous and M.dtype == np.float64
-    _load().orc_tridiagonalize(M.shape[0], _ptr(M), M.shape[0], _ptr(d), _ptr(e), nsteps)
+    lib = load_omp() if omp else _load()
+    lib.orc_tridiagonalize(M.shape[0], _ptr(M), M.shape[0], _ptr(d), _ptr(e), nsteps)
 
 
 def pivmin(e) -> float:
@@ -170,14 +211,16 @@ def bisect(d, e, rtol: float = 1e-14, maxit: int = 200, return_noconv: bool = Fa
     return (out[:n], nc) if return_noconv else out[:n]
 
 
-def bisect_range(d, e, k0: int, k1: int, rtol: float = 1e-14, maxit: int = 200):
-    """Eigenvalues k0 <= k < k1 (ascending indices) of T(d, e) by bisection."""
+def bisect_range(d, e, k0: int, k1: int, rtol: float = 1e-14, maxit: int = 200, omp: bool = False):
+    """Eigenvalues k0 <= k < k1 (ascending indices) of T(d, e) by bisection
+    (omp: the OpenMP build, same results)."""
     d = np.ascontiguousarray(d, dtype=np.float64)
     n = d.size
     ee = np.zeros(max(n, 1))
     ee[: n - 1] = np.asarray(e, dtype=np.float64)[: n - 1]
     out = np.zeros(max(k1 - k0, 1))
-    _load().orc_bisect_range(n, _ptr(d), _ptr(ee), float(rtol), int(maxit), int(k0), int(k1), _ptr(out))
+    lib = load_omp() if omp else _load()
+    lib.orc_bisect_range(n, _ptr(d), _ptr(ee), float(rtol), int(maxit), int(k0), int(k1), _ptr(out))
     return out[: k1 - k0]
 
 

@@ -96,6 +96,9 @@ void orc_tridiagonalize(int n, double *A, int lda, double *d, double *e, int nst
     if (nsteps >= 0 && nsteps < last) last = nsteps;
     double *v = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double *p = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#ifdef _OPENMP
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#endif
     for (int j = 0; j < last; ++j) {
         int m = n - j - 1; /* length of x = A[j+1:n, j] */
         double *x = &A[IDX(j + 1, j, lda)];
@@ -111,6 +114,7 @@ void orc_tridiagonalize(int n, double *A, int lda, double *d, double *e, int nst
         /* p = tau * A22 v, A22 = A[j+1:n, j+1:n] read from its lower triangle */
         double *A22 = &A[IDX(j + 1, j + 1, lda)];
         for (int i = 0; i < m; ++i) p[i] = 0.0;
+#ifndef _OPENMP
         for (int c = 0; c < m; ++c) {
             double vc = v[c];
             double acc = A22[IDX(c, c, lda)] * vc;
@@ -122,11 +126,37 @@ void orc_tridiagonalize(int n, double *A, int lda, double *d, double *e, int nst
             }
             p[c] += acc + pc;
         }
+#else
+        /* The same sums in the same order per output, with independent
+         * outputs on separate cores: p[r] first gathers A22[r, c] v_c for
+         * c = 0 .. r-1 in increasing c, then adds acc_r + pc_r. */
+        {
+#pragma omp parallel for schedule(dynamic, 32)
+            for (int c = 0; c < m; ++c) {
+                double pc = 0.0;
+                for (int r = c + 1; r < m; ++r) pc += A22[IDX(r, c, lda)] * v[r];
+                tmp[c] = A22[IDX(c, c, lda)] * v[c] + pc;
+            }
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int r0 = 0; r0 < m; r0 += 64) {
+                int r1 = r0 + 64 < m ? r0 + 64 : m;
+                for (int c = 0; c < r1 - 1; ++c) {
+                    double vc = v[c];
+                    int rs = c + 1 > r0 ? c + 1 : r0;
+                    for (int r = rs; r < r1; ++r) p[r] += A22[IDX(r, c, lda)] * vc;
+                }
+                for (int r = r0; r < r1; ++r) p[r] += tmp[r];
+            }
+        }
+#endif
         for (int i = 0; i < m; ++i) p[i] *= tau;
         double ptv = 0.0;
         for (int i = 0; i < m; ++i) ptv += p[i] * v[i];
         double half = 0.5 * tau * ptv;
         for (int i = 0; i < m; ++i) p[i] -= half * v[i]; /* p now holds w */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
         for (int c = 0; c < m; ++c) {
             double vc = v[c], wc = p[c];
             for (int r = c; r < m; ++r)
@@ -137,6 +167,9 @@ void orc_tridiagonalize(int n, double *A, int lda, double *d, double *e, int nst
     if (n >= 2 && (nsteps < 0 || nsteps >= n - 2)) e[n - 2] = A[IDX(n - 1, n - 2, lda)];
     free(v);
     free(p);
+#ifdef _OPENMP
+    free(tmp);
+#endif
 }
 
 /*
@@ -342,6 +375,9 @@ int orc_bisect_range(int n, const double *d, const double *e, double rtol, int m
     gu += pad;
     double atol = rtol * tnorm;
     int noconv = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : noconv)
+#endif
     for (int k = k0; k < k1; ++k) {
         double lo = gl, hi = gu;
         int it = 0;

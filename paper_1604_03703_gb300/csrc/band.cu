@@ -24,7 +24,7 @@
 // its sweep before taking another, so every awaited sweep is held by a
 // running CTA: the waits cannot deadlock.  Every wait is capped; on expiry
 // the kernel latches SEV_ERR_TIMEOUT and returns.
-#include "common.cuh"
+#include "regtile.cuh"
 
 #ifdef SEV_TRACE
 static __device__ long long *sev_btrace = nullptr;
@@ -78,9 +78,12 @@ __device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, i
     }
     AB[d + (size_t)c * ldab] = v;
 }
+// Shared memory of one chase: U, U T, the block X being updated, W, T, a
+// small product Z, tau, the double-buffered reflector of the register QR and
+// a reduction scratch.
 template <typename T>
 struct ChaseSmem {
-    T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau;
+    T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau, *vs;
     double *red;
     int ldb1, ldh1;
     __device__ ChaseSmem(unsigned char *base, int b, int h) {
@@ -93,7 +96,8 @@ struct ChaseSmem {
         Ts = Ws + (size_t)ldb1 * h;
         Zs = Ts + (size_t)ldh1 * h;
         tau = Zs + (size_t)ldh1 * h;
-        size_t off = (size_t)((unsigned char *)(tau + h) - base);
+        vs = tau + h;
+        size_t off = (size_t)((unsigned char *)(vs + 2 * 128) - base);
         off = (off + 15) & ~(size_t)15;
         red = (double *)(base + off);
     }
@@ -102,14 +106,20 @@ struct ChaseSmem {
 template <typename T>
 size_t band_smem_bytes(int b, int h) {
     const size_t ldb1 = b + 1, ldh1 = h + 1;
-    size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h;
+    size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h + 2 * 128;
     size_t bytes = e * sizeof(T);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + 32 * sizeof(double);
 }
 
-// One chase (i, j) performed by the whole CTA.
-template <typename T>
+// Register tile of the chase QR (8 warps): rows up to 32 R (R = 0: the
+// shared-memory cta_qr), columns up to 8 Q.
+__host__ __device__ constexpr int chase_tile_r(int b) { return b <= 32 ? 1 : (b <= 64 ? 2 : (b <= 128 ? 4 : 0)); }
+__host__ __device__ constexpr int chase_tile_q(int h) { return h <= 8 ? 1 : (h <= 16 ? 2 : (h <= 32 ? 4 : (h <= 64 ? 8 : 0))); }
+
+// One chase (i, j) performed by the whole CTA.  RQ, QQ > 0: the n_r x h QR
+// runs on a register tile of 32 RQ x 8 QQ (reg_qr); 0: on shared memory.
+template <typename T, int RQ, int QQ>
 __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, ChaseSmem<T> &S, int *bad) {
     const int o_qr_r = (i - 1) * h + (j - 1) * b + h;
     int o_qr_c, o_v, o_up_c, lim;
@@ -130,33 +140,66 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     const int tid = threadIdx.x, nt = blockDim.x;
 
     BTRACE(0);
-    // 1. QR of the n_r x h block
-    batched_copy<T>(
-        n_r * h, tid, nt, [&](int k) { return bld(AB, ldab, n, o_qr_r + k % n_r, o_qr_c + k / n_r, bad); },
-        [&](int k, T v) { S.Xs[k % n_r + (size_t)(k / n_r) * ldb1] = v; });
-    __syncthreads();
-    BTRACE(1);
-    const int nr = cta_qr(n_r, h, S.Xs, ldb1, S.tau, S.red);
-    BTRACE(2);
-    // 2. B[qr rows, qr cols] = [R; 0]
-    for (int idx = tid; idx < n_r * h; idx += nt) {
-        const int r = idx % n_r, c = idx / n_r;
-        const T v = (r <= c) ? S.Xs[r + (size_t)c * ldb1] : T(0);
-        bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, v, bad);
-    }
-    if (nr == 0) {
+    int nr;
+    if constexpr (RQ > 0) {
+        // 1. QR of the n_r x h block in registers (lane rows, warp-cyclic columns)
+        const int warp = tid >> 5, lane = tid & 31;
+        T a[QQ][RQ];
+#pragma unroll
+        for (int q = 0; q < QQ; ++q)
+#pragma unroll
+            for (int t = 0; t < RQ; ++t) {
+                const int r = lane + 32 * t, c = warp + 8 * q;
+                a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
+            }
+        BTRACE(1);
+        nr = reg_qr<T, RQ, QQ, 8>(a, n_r, h, 0, S.vs, S.tau);
+        BTRACE(2);
+        // 2. B[qr rows, qr cols] = [R; 0]; U explicit into shared memory
+#pragma unroll
+        for (int q = 0; q < QQ; ++q)
+#pragma unroll
+            for (int t = 0; t < RQ; ++t) {
+                const int r = lane + 32 * t, c = warp + 8 * q;
+                if (r < n_r && c < h) {
+                    bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, r <= c ? a[q][t] : T(0), bad);
+                    if (c < nr) S.Us[r + (size_t)c * ldb1] = r < c ? T(0) : (r == c ? T(1) : a[q][t]);
+                }
+            }
+        if (nr == 0) {
+            __syncthreads();
+            return;
+        }
+    } else {
+        // 1. QR of the n_r x h block
+        batched_copy<T>(
+            n_r * h, tid, nt, [&](int k) { return bld(AB, ldab, n, o_qr_r + k % n_r, o_qr_c + k / n_r, bad); },
+            [&](int k, T v) { S.Xs[k % n_r + (size_t)(k / n_r) * ldb1] = v; });
         __syncthreads();
-        return;
+        BTRACE(1);
+        nr = cta_qr(n_r, h, S.Xs, ldb1, S.tau, S.red);
+        BTRACE(2);
+        // 2. B[qr rows, qr cols] = [R; 0]
+        for (int idx = tid; idx < n_r * h; idx += nt) {
+            const int r = idx % n_r, c = idx / n_r;
+            const T v = (r <= c) ? S.Xs[r + (size_t)c * ldb1] : T(0);
+            bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, v, bad);
+        }
+        if (nr == 0) {
+            __syncthreads();
+            return;
+        }
+        cta_extract_u(n_r, nr, nr, S.Xs, ldb1, S.Us, ldb1);
     }
-    // 3. U, T and U T (T from G = U^T U by one warp's recurrence when h <= 32)
-    cta_extract_u(n_r, nr, nr, S.Xs, ldb1, S.Us, ldb1);
+    // 3. T and U T (T from G = U^T U by one warp's recurrence when h <= 32)
     if (nr <= 32) {
         __syncthreads();
         cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Us, ldb1, T(0), S.Zs, ldh1);
         __syncthreads();
         form_t_from_g(nr, S.Zs, ldh1, S.tau, S.Ts, ldh1);
     } else {
-        cta_form_t(n_r, nr, S.Xs, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
+        __syncthreads();
+        cta_form_t(n_r, nr, S.Us, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
     }
     cta_gemm<T, false, false>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, T(0), S.UTs, ldb1);
     __syncthreads();
@@ -282,7 +325,7 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     BTRACE(5);
 }
 
-template <typename T>
+template <typename T, int RQ, int QQ>
 __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int ldab, int b, int h, int nsweeps,
                                                                int *progress, int *sweep_ctr, int *err) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -321,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int 
                 __syncthreads();
                 if (s_abort) return;
             }
-            band_chase(AB, ldab, n, b, h, i, j, S, &s_bad);
+            band_chase<T, RQ, QQ>(AB, ldab, n, b, h, i, j, S, &s_bad);
             __syncthreads();
             // the release store orders the CTA's writes (made visible to
             // thread 0 by the barrier above) before the progress flag
@@ -351,9 +394,20 @@ int launch_band_to_band(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, void 
     int *ctr = c.take<int>(1);
     SEV_CUDA(cudaMemsetAsync(progress, 0, sizeof(int) * ((size_t)nsweeps + 1), hd->stream));
     SEV_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), hd->stream));
-    SEV_CUDA(cudaFuncSetAttribute(band_chase_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int RQ = chase_tile_r(b), QQ = chase_tile_q(h);
+    auto kern = band_chase_kernel<T, 0, 0>;
+    if (RQ == 1 && QQ == 1) kern = band_chase_kernel<T, 1, 1>;
+    if (RQ == 1 && QQ == 2) kern = band_chase_kernel<T, 1, 2>;
+    if (RQ == 2 && QQ == 1) kern = band_chase_kernel<T, 2, 1>;
+    if (RQ == 2 && QQ == 2) kern = band_chase_kernel<T, 2, 2>;
+    if (RQ == 2 && QQ == 4) kern = band_chase_kernel<T, 2, 4>;
+    if (RQ == 4 && QQ == 1) kern = band_chase_kernel<T, 4, 1>;
+    if (RQ == 4 && QQ == 2) kern = band_chase_kernel<T, 4, 2>;
+    if (RQ == 4 && QQ == 4) kern = band_chase_kernel<T, 4, 4>;
+    if (RQ == 4 && QQ == 8) kern = band_chase_kernel<T, 4, 8>;
+    SEV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, band_chase_kernel<T>, kThreads, smem));
+    SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
     int grid = hd->sm_count * per_sm;
     // sweep i runs ~3 chases behind sweep i - 1, so about J/3 sweeps (J the
@@ -362,8 +416,7 @@ int launch_band_to_band(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, void 
     const int busy = band_num_chases(n, b, h, 0) / 3 + 8;
     if (grid > busy) grid = busy;
     if (grid > nsweeps) grid = nsweeps;
-    SEV_LAUNCH(hd, K_BAND_CHASE, band_chase_kernel<T>, grid, kThreads, smem, n, AB, ldab, b, h, nsweeps, progress,
-               ctr, hd->d_err);
+    SEV_LAUNCH(hd, K_BAND_CHASE, kern, grid, kThreads, smem, n, AB, ldab, b, h, nsweeps, progress, ctr, hd->d_err);
     return SEV_OK;
 }
 

@@ -588,6 +588,9 @@ __device__ void cta_gemm(int M, int N, int K, T alpha, const T *A, int lda, cons
             nv[i] = 4 * nb + i < N;
         }
         T acc[4][4] = {};
+        // unrolled so later k's loads issue ahead of the FMAs (each output's
+        // sum keeps its k order: the results do not change)
+#pragma unroll 4
         for (int k = 0; k < K; ++k) {
             T a[4], bb[4];
 #pragma unroll

@@ -1,0 +1,238 @@
+// regtile.cuh -- register-tile primitives of the Householder kernels: a CTA of
+// NW warps holds a (32 R) x (NW Q) block with lane l of warp w keeping
+// a[q][t] = M(l + 32 t, w + NW q) (columns dealt to the warps cyclically, the
+// rows of a column inside one warp).  reg_qr is a Householder QR with one
+// barrier per column and a one-column lookahead; reg_apply_all applies a
+// stored sequence of reflectors to warp-private columns without barriers.
+// Used by the tree QR of the panel factorisation (panel_reg.cu) and by the
+// QR step of every band chase (band.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace sev {
+
+template <typename T>
+__device__ __forceinline__ T fmat(T a, T b, T c);
+template <>
+__device__ __forceinline__ float fmat<float>(float a, float b, float c) {
+    return fmaf(a, b, c);
+}
+template <>
+__device__ __forceinline__ double fmat<double>(double a, double b, double c) {
+    return fma(a, b, c);
+}
+
+// x[t] for a run-time t without dynamic register indexing.
+template <int R, typename T>
+__device__ __forceinline__ T rsel(const T (&x)[R], int t) {
+    T r = x[0];
+#pragma unroll
+    for (int i = 1; i < R; ++i)
+        if (i == t) r = x[i];
+    return r;
+}
+
+// Does the 32-row block t hold a row where reflector k can be nonzero?
+// bstack = 0: dense (rows >= k); bstack = b (a multiple of 32): a stack of
+// upper triangles of height b (row k of the first, rows 0..k of the others).
+__device__ __forceinline__ bool rblk_active(int t, int k, int bstack) {
+    const int r0 = 32 * t;
+    if (bstack == 0) return r0 + 31 >= k;
+    if (r0 <= k && k < r0 + 32) return true;
+    return r0 >= bstack && (r0 % bstack) <= k;
+}
+
+// Columns q of `a` in qmask (warp-uniform) <- H a, H = I - tau v v^T, v given
+// per lane row in vr (zero outside the active blocks).  The dot products of
+// all selected columns are reduced together so their shuffle chains overlap.
+template <typename T, int R, int Q>
+__device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const bool (&act)[R], T tau,
+                                          unsigned qmask) {
+    T d[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        d[q] = T(0);
+        if ((qmask >> q) & 1u) {
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (act[t]) d[q] = fmat(vr[t], a[q][t], d[q]);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if ((qmask >> q) & 1u) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        if ((qmask >> q) & 1u) {
+            const T s = tau * d[q];
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (act[t]) a[q][t] = fmat(-s, vr[t], a[q][t]);
+        }
+    }
+}
+
+// Reflector of rows k..m-1 of the column x (one warp; lane rows lane + 32 t;
+// rows >= m are zero).  On return x holds beta at row k and v below it (rows
+// < k untouched), vout[0 .. 32R) receives v (0 above k, 1 at k) and the
+// return value is tau.  All lanes evaluate the scalars (no broadcast).
+template <typename T, int R>
+__device__ __forceinline__ T reg_house(T (&x)[R], int k, T *vout) {
+    const int lane = threadIdx.x & 31;
+    const T alpha = __shfl_sync(0xffffffffu, rsel<R>(x, k >> 5), k & 31);
+    T tau, beta, inv;
+    if constexpr (sizeof(T) == 4) {
+        F2 a0{0.f, 0.f}, a1{0.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int row = lane + 32 * t;
+            if (row > k) {
+                if (t & 1)
+                    f2_add_sq(a1, (float)x[t]);
+                else
+                    f2_add_sq(a0, (float)x[t]);
+            }
+        }
+        const F2 acc = warp_sum_f2(f2_add(a0, a1));
+        float tf, bf, iv;
+        house_scalars_f2((float)alpha, acc, &tf, &bf, &iv);
+        tau = (T)tf;
+        beta = (T)bf;
+        inv = (T)iv;
+    } else {
+        double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            const int row = lane + 32 * t;
+            if (row > k) {
+                if (t & 1)
+                    s1 = fma((double)x[t], (double)x[t], s1);
+                else
+                    s0 = fma((double)x[t], (double)x[t], s0);
+            }
+        }
+        const double ssq = warp_sum(s0 + s1);
+        const double al = (double)alpha;
+        double td, bd, id;
+        if ((ssq != 0.0 && ssq < 1e-280) || !(ssq < 1e300) || fabs(al) > 1e150 || (al != 0.0 && fabs(al) < 1e-140)) {
+            // rare: rescale by an exact power of two so the squares neither
+            // overflow nor underflow
+            double amax = fabs(al);
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (lane + 32 * t > k) amax = fmax(amax, fabs((double)x[t]));
+            amax = warp_max(amax);
+            int e2;
+            frexp(amax, &e2);
+            const double sc = ldexp(1.0, -e2);
+            double a2 = 0.0;
+#pragma unroll
+            for (int t = 0; t < R; ++t)
+                if (lane + 32 * t > k) {
+                    const double y = (double)x[t] * sc;
+                    a2 = fma(y, y, a2);
+                }
+            a2 = warp_sum(a2);
+            house_scalars(al * sc, a2, &td, &bd, &id);
+            bd /= sc;
+            id *= sc;
+        } else {
+            house_scalars(al, ssq, &td, &bd, &id);
+        }
+        tau = (T)td;
+        beta = (T)bd;
+        inv = (T)id;
+    }
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        const int row = lane + 32 * t;
+        if (row == k) {
+            x[t] = beta;
+            vout[row] = T(1);
+        } else if (row > k) {
+            if (tau != T(0)) x[t] = x[t] * inv;
+            vout[row] = x[t];
+        } else {
+            vout[row] = T(0);
+        }
+    }
+    return tau;
+}
+
+// Householder QR of the m x nc block held in `a` (m <= 32R, nc <= 16Q; rows
+// >= m and columns >= nc zero), r = min(nc, m - 1) reflectors.  On return
+// column c holds R above and on the diagonal and v_c below it (unit
+// diagonal implicit); taus[c] = tau_c.  vs: 2 x 32R shared scratch.
+template <typename T, int R, int Q, int NW>
+__device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = nc < m - 1 ? nc : m - 1;
+    if (r <= 0) {
+        __syncthreads();
+        return 0;
+    }
+    if (warp == 0) {
+        const T t0 = reg_house<T, R>(a[0], 0, vs);
+        if (lane == 0) taus[0] = t0;
+    }
+    __syncthreads();
+    for (int k = 0; k < r; ++k) {
+        const T *v = vs + (k & 1) * (32 * R);
+        const T tk = taus[k];
+        bool act[R];
+        T vr[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            act[t] = rblk_active(t, k, bstack);
+            vr[t] = act[t] ? v[lane + 32 * t] : T(0);
+        }
+        unsigned mine = 0;
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int c = warp + NW * q;
+            if (c > k && c < nc) mine |= 1u << q;
+        }
+        const int k1 = k + 1;
+        if (k1 < nc && (k1 % NW) == warp) {
+            // lookahead: column k+1 first, then reflector k+1 from it
+            const int q1 = k1 / NW;
+            if (tk != T(0)) reg_apply<T, R, Q>(a, vr, act, tk, 1u << q1);
+            if (k1 < r) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+                    if (q == q1) {
+                        const T t1 = reg_house<T, R>(a[q], k1, vs + (k1 & 1) * (32 * R));
+                        if (lane == 0) taus[k1] = t1;
+                    }
+            }
+            mine &= ~(1u << q1);
+        }
+        if (tk != T(0) && mine) reg_apply<T, R, Q>(a, vr, act, tk, mine);
+        __syncthreads();
+    }
+    return r;
+}
+
+// M <- H_0 H_1 ... H_{nr-1} M: reflectors explicit in Vs (column k at
+// Vs[k * ldv], rows 0 .. 32R), scalars in taus; columns of M in qmask.
+template <typename T, int R, int Q>
+__device__ void reg_apply_all(T (&m)[Q][R], const T *Vs, int ldv, const T *taus, int nr, int bstack, unsigned qmask) {
+    const int lane = threadIdx.x & 31;
+    for (int k = nr - 1; k >= 0; --k) {
+        const T tk = taus[k];
+        if (tk == T(0)) continue;
+        bool act[R];
+        T vr[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+            act[t] = rblk_active(t, k, bstack);
+            vr[t] = act[t] ? Vs[(size_t)k * ldv + lane + 32 * t] : T(0);
+        }
+        reg_apply<T, R, Q>(m, vr, act, tk, qmask);
+    }
+}
+
+}  // namespace sev

@@ -44,3 +44,27 @@ def test_oracle_sample_extrapolates(orc):
     r = bench.oracle_sample(A, 96, 1e-9, 0.2)
     assert r["seconds_extrapolated"] > 0 and r["value"] > 0
     assert "Householder steps" in r["sample"]
+
+
+def test_oracle_openmp_build_gives_the_same_bits(orc):
+    """The all-cores CPU baseline runs the oracle compiled with OpenMP; its
+    results must be the serial oracle's, bit for bit."""
+    if orc.load_omp() is None:
+        pytest.skip("no OpenMP runtime")
+    for n in (5, 130, 517):
+        A = I.semicircle(n, 40 + n)
+        d1, e1 = orc.tridiagonalize(A)
+        M = np.array(A, order="F", copy=True)
+        d2, e2 = np.zeros(n), np.zeros(n)
+        orc.tridiagonalize_inplace(M, d2, e2, -1, omp=True)
+        np.testing.assert_array_equal(d1, d2)
+        np.testing.assert_array_equal(e1, e2[: n - 1])
+        np.testing.assert_array_equal(orc.bisect_range(d1, e1, 0, n, 1e-14, omp=True), orc.bisect(d1, e1, 1e-14))
+
+
+def test_oracle_sample_all_cores(orc):
+    A = I.semicircle(96, 4)
+    r = bench.oracle_sample(A, 96, 1e-9, 0.2, omp=True)
+    if r is None:
+        pytest.skip("no OpenMP runtime")
+    assert r["cores"] == bench.host_cores() and r["value"] > 0
