@@ -809,6 +809,9 @@ void batch_pack_mat(void *dst, void *A, double *eigs, int n, int lda);
 template <typename T>
 int launch_batch_fill(sev_ctx *h, int count, const void *mats, unsigned long long seed);
 
+// update.cu: Y = sum of the K-split partial products (N x b each, split order)
+int launch_symm_reduce(sev_ctx *h, int N, int b, int splits, const float *part, float *Y);
+
 // panel.cu + panel_reg.cu + update.cu
 // Buffers of the register-resident panel factorisation (panel_reg.cu).
 template <typename T>

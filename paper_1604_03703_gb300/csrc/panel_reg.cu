@@ -150,10 +150,13 @@ __global__ void __launch_bounds__(kRegThreads, 1)
     const int rows = nc * b;
     const int nr = nref[node];
     const T *Y = Ylev + (size_t)p * ystride;
-    for (int idx = threadIdx.x; idx < nr * 32 * R; idx += blockDim.x) {
-        const int k = idx / (32 * R), r = idx % (32 * R);
-        Vs[idx] = r < rows ? Y[r + (size_t)k * rows] : T(0);
-    }
+    batched_copy<T>(
+        nr * 32 * R, threadIdx.x, blockDim.x,
+        [&](int idx) {
+            const int k = idx / (32 * R), r = idx % (32 * R);
+            return r < rows ? Y[r + (size_t)k * rows] : T(0);
+        },
+        [&](int idx, T v) { Vs[idx] = v; });
     for (int k = threadIdx.x; k < nr; k += blockDim.x) taus[k] = tau[(size_t)node * b + k];
     const T *Zn = Zbuf + (size_t)node * b * b;
     T m[Q][R];
@@ -197,10 +200,13 @@ __global__ void __launch_bounds__(kRegThreads, 1)
     const int row0 = rleaf_row0(N, L, l);
     const int rows = rleaf_row0(N, L, l + 1) - row0;
     const int nr = nref[l];
-    for (int idx = threadIdx.x; idx < nr * 32 * R; idx += blockDim.x) {
-        const int k = idx / (32 * R), r = idx % (32 * R);
-        Vs[idx] = r < rows ? Y[(size_t)(row0 + r) + (size_t)k * ldy] : T(0);
-    }
+    batched_copy<T>(
+        nr * 32 * R, threadIdx.x, blockDim.x,
+        [&](int idx) {
+            const int k = idx / (32 * R), r = idx % (32 * R);
+            return r < rows ? Y[(size_t)(row0 + r) + (size_t)k * ldy] : T(0);
+        },
+        [&](int idx, T v) { Vs[idx] = v; });
     for (int k = threadIdx.x; k < nr; k += blockDim.x) taus[k] = tau[(size_t)l * b + k];
     const T *Zl = Zbuf + (size_t)l * b * b;
     T m[Q][R];
@@ -446,8 +452,8 @@ static int reg_panel_run(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, c
         SEV_LAUNCH(h, K_TSQR_TREE, (rtsqr_node_qr_kernel<T, R, Q>), cnt[lev], kRegThreads, 0, b, cnt[lev - 1],
                    off[lev - 1], off[lev], B.Rbuf, Ylev, ystride, B.tau, B.nref);
     }
-    // the way down: slices of 16 x 2 columns per CTA (more CTAs for the short upper levels)
-    constexpr int QA = 2;
+    // the way down: slices of 16 x 4 columns per CTA
+    constexpr int QA = 4;
     const int slices = (b + kRegWarps * QA - 1) / (kRegWarps * QA);
     const size_t s_apply = sizeof(T) * ((size_t)32 * R * b + b);
     SEV_CUDA(cudaFuncSetAttribute(rtsqr_node_apply_kernel<T, R, QA>, cudaFuncAttributeMaxDynamicSharedMemorySize,

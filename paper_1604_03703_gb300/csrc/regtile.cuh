@@ -197,17 +197,27 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
         }
         const int k1 = k + 1;
         if (k1 < nc && (k1 % NW) == warp) {
-            // lookahead: column k+1 first, then reflector k+1 from it
+            // lookahead: column k+1 first (copied out of the tile, so the
+            // reflector code is emitted once), then reflector k+1 from it
             const int q1 = k1 / NW;
-            if (tk != T(0)) reg_apply<T, R, Q>(a, vr, act, tk, 1u << q1);
-            if (k1 < r) {
+            T x[1][R];
 #pragma unroll
-                for (int q = 0; q < Q; ++q)
-                    if (q == q1) {
-                        const T t1 = reg_house<T, R>(a[q], k1, vs + (k1 & 1) * (32 * R));
-                        if (lane == 0) taus[k1] = t1;
-                    }
+            for (int t = 0; t < R; ++t) x[0][t] = a[0][t];
+#pragma unroll
+            for (int q = 1; q < Q; ++q)
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+                    if (q == q1) x[0][t] = a[q][t];
+            if (tk != T(0)) reg_apply<T, R, 1>(x, vr, act, tk, 1u);
+            if (k1 < r) {
+                const T t1 = reg_house<T, R>(x[0], k1, vs + (k1 & 1) * (32 * R));
+                if (lane == 0) taus[k1] = t1;
             }
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+#pragma unroll
+                for (int t = 0; t < R; ++t)
+                    if (q == q1) a[q][t] = x[0][t];
             mine &= ~(1u << q1);
         }
         if (tk != T(0) && mine) reg_apply<T, R, Q>(a, vr, act, tk, mine);

@@ -26,6 +26,10 @@ template <typename T>
 int tc_syr2k(sev_ctx *h, int N, int b, T *A22, int lda, const T *U, const T *V, void *ws);
 template <typename T>
 size_t tc_workspace(int n, int b);
+template <typename T>
+int tc_symm_supported(sev_ctx *h, int N, int b, const T *A22, int lda);
+template <typename T>
+int tc_symm(sev_ctx *h, int N, int b, const T *A22, int lda, const T *U, T *Y, T *ypart, int max_splits, void *ws);
 
 constexpr int BM = 64, BN = 64, BK = 16, PADT = 4;
 
@@ -293,6 +297,13 @@ __global__ void symm_reduce_kernel(int N, int b, int splits, const float *__rest
     }
 }
 
+int launch_symm_reduce(sev_ctx *h, int N, int b, int splits, const float *part, float *Y) {
+    int g = (int)(((size_t)N * b + 255) / 256);
+    if (g > h->sm_count * 8) g = h->sm_count * 8;
+    SEV_LAUNCH(h, K_SYMM, symm_reduce_kernel, g, 256, 0, N, b, splits, part, (size_t)N * b, Y, N);
+    return SEV_OK;
+}
+
 // C = alpha * A B + beta * D, A (M x K, m contiguous), B (K x Nc, k contiguous, ld ldb).
 // Used for X = Y T and V = 1/2 U Zm - X.
 template <typename T>
@@ -478,7 +489,10 @@ int launch_full_to_band(sev_ctx *h, int n, T *A, int lda, int b, T *AB, int ldab
         if (rc) return rc;
         const bool tc = tc_update_supported<T>(h, N, b);
         // Y = A22 U
-        if (sizeof(T) == 4 && lda % 4 == 0 && ((uintptr_t)A22 & 15) == 0) {
+        if (tc_symm_supported<T>(h, N, b, A22, lda)) {
+            rc = tc_symm<T>(h, N, b, A22, lda, B.U, B.Y, B.ypart, kSymmMaxSplits, B.tc_ws);
+            if (rc) return rc;
+        } else if (sizeof(T) == 4 && lda % 4 == 0 && ((uintptr_t)A22 & 15) == 0) {
             // split K until the grid covers ~2 CTAs per SM
             const int mt = (N + SBM - 1) / SBM, nt = (b + SBN - 1) / SBN;
             int splits = 1;

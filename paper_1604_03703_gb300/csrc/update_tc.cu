@@ -294,6 +294,283 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tmem_dealloc(tmem, 128);
 }
 
+// ------------------------------------------------------ symmetric product
+// Y = A22 U, the first product of the V formation (W = A22 U in Eq. 4.1 /
+// Algorithm 4.1), for FP32 data on the tensor cores in BF16x3:
+// Y ~ Ah Uh + Ah Ul + Al Uh (hi/lo splits as in split_bf16x3_kernel; the
+// Al Ul term, ~2^-16 relative, dropped), FP32 accumulation in TMEM.
+//
+// CTA (I, s) computes rows [128 I, 128 I + 128) of Y over the 64-wide
+// K-blocks of split s.  A22 is stored in its lower triangle only, so the A
+// tile of K-block kb comes from whichever triangle holds it: below the
+// diagonal block, a 128 (rows) x 64 box of its columns (TMA, rows
+// contiguous); above it, a 64 x 128 box of the stored lower part read as
+// rows (A(i, k) = A(k, i); TMA, k contiguous); the two K-blocks that meet the
+// diagonal are loaded element by element.  Converter warps split every FP32
+// tile into BF16 hi and lo tiles in the K-major, 128-byte-swizzled layout
+// of the MMA operand (16-byte chunk c of row i at chunk c ^ (i mod 8)); the
+// U tiles, split once per panel, arrive by TMA in that layout.
+// Warps: 0 TMA producer, 1-4 converters and epilogue, 5 MMA issuer.  Every
+// wait is time-capped; a CTA whose wait runs out latches SEV_ERR_TIMEOUT,
+// lets the copies and MMAs it issued finish, frees its TMEM and returns.
+constexpr int kSyRaw = 2;                   // FP32 tile stages
+constexpr int kSyCvt = 2;                   // converted operand stages
+constexpr int kSyRawBytes = 128 * 64 * 4;   // one FP32 tile
+constexpr int kSyThreads = 192;
+__host__ __device__ constexpr int sy_cvt_bytes(int bn) { return 2 * 128 * 128 + 2 * bn * 128; }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Eight FP32 values of row i, K-chunk ch: BF16 hi and lo parts into the
+// swizzled hi / lo tiles (128-byte rows).
+__device__ __forceinline__ void sy_store_chunk(unsigned char *hi_t, unsigned char *lo_t, int i, int ch,
+                                               const float (&v)[8]) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const __nv_bfloat16 h0 = __float2bfloat16_rn(v[2 * j]), h1 = __float2bfloat16_rn(v[2 * j + 1]);
+        const __nv_bfloat16 l0 = __float2bfloat16_rn(v[2 * j] - __bfloat162float(h0));
+        const __nv_bfloat16 l1 = __float2bfloat16_rn(v[2 * j + 1] - __bfloat162float(h1));
+        h[j] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+        l[j] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    }
+    const int off = i * 128 + ((ch ^ (i & 7)) << 4);
+    *reinterpret_cast<uint4 *>(hi_t + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(lo_t + off) = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kSyThreads, 1)
+    symm_tc_kernel(const __grid_constant__ CUtensorMap mapAc, const __grid_constant__ CUtensorMap mapAr,
+                   const __grid_constant__ CUtensorMap mapUh, const __grid_constant__ CUtensorMap mapUl,
+                   const float *__restrict__ A, int lda, int N, int kb_per_split, float *__restrict__ Ypart,
+                   size_t split_stride, int *err) {
+    constexpr int kCvt = sy_cvt_bytes(BN);
+    constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((128u >> 4) << 24);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *raw = smem;
+    unsigned char *cvt = raw + kSyRaw * kSyRawBytes;
+    __shared__ __align__(8) uint64_t raw_full[kSyRaw], raw_empty[kSyRaw], u_full[kSyCvt], a_full[kSyCvt],
+        cvt_empty[kSyCvt], done;
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_fail, s_raw_issued, s_u_issued, s_mma_done;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int I = blockIdx.x, s = blockIdx.y;
+    const int nkb = (N + 63) / 64;
+    const int kb0 = s * kb_per_split, kb1 = min(nkb, kb0 + kb_per_split);
+    // 0: below the diagonal block, 1: above it, 2: meets the diagonal
+    auto kind = [&](int kb) { return 64 * kb + 64 <= 128 * I ? 0 : (64 * kb >= 128 * I + 128 ? 1 : 2); };
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kSyRaw; ++q) {
+            mbar_init(&raw_full[q], 1);
+            mbar_init(&raw_empty[q], 4);
+        }
+        for (int q = 0; q < kSyCvt; ++q) {
+            mbar_init(&u_full[q], 1);
+            mbar_init(&a_full[q], 4);
+            mbar_init(&cvt_empty[q], 1);
+        }
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+        s_raw_issued = 0;
+        s_u_issued = 0;
+        s_mma_done = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_base, BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0 && lane == 0) {
+        // ---- TMA producer: FP32 A tiles (off-diagonal K-blocks), U hi/lo tiles
+        int r = 0, c = 0;
+        for (int kb = kb0; kb < kb1; ++kb, ++c) {
+            const int k = kind(kb);
+            if (k != 2) {
+                const int sr = r % kSyRaw, ur = r / kSyRaw;
+                if (ur > 0 && !mbar_wait(&raw_empty[sr], (ur - 1) & 1, err)) {
+                    s_fail = 1;
+                    break;
+                }
+                mbar_expect_tx(&raw_full[sr], kSyRawBytes);
+                if (k == 0)
+                    tma_load_2d(raw + sr * kSyRawBytes, &mapAc, 128 * I, 64 * kb, &raw_full[sr]);
+                else
+                    tma_load_2d(raw + sr * kSyRawBytes, &mapAr, 64 * kb, 128 * I, &raw_full[sr]);
+                ++r;
+                s_raw_issued = r;
+            }
+            const int sc = c % kSyCvt, uc = c / kSyCvt;
+            if (uc > 0 && !mbar_wait(&cvt_empty[sc], (uc - 1) & 1, err)) {
+                s_fail = 1;
+                break;
+            }
+            unsigned char *cs = cvt + sc * kCvt;
+            mbar_expect_tx(&u_full[sc], 2 * BN * 128);
+            tma_load_2d(cs + 32768, &mapUh, 64 * kb, 0, &u_full[sc]);
+            tma_load_2d(cs + 32768 + BN * 128, &mapUl, 64 * kb, 0, &u_full[sc]);
+            s_u_issued = c + 1;
+        }
+    } else if (warp >= 1 && warp <= 4) {
+        // ---- converters: FP32 tile -> BF16 hi / lo operand tiles
+        const int t = threadIdx.x - 32;  // 0 .. 127
+        int r = 0, c = 0;
+        for (int kb = kb0; kb < kb1; ++kb, ++c) {
+            const int k = kind(kb);
+            const int sc = c % kSyCvt, uc = c / kSyCvt;
+            if (uc > 0 && !mbar_wait(&cvt_empty[sc], (uc - 1) & 1, err)) {
+                s_fail = 1;
+                break;
+            }
+            unsigned char *ah = cvt + sc * kCvt, *al = ah + 16384;
+            if (k == 2) {
+                const int gi = 128 * I + t;
+#pragma unroll 1
+                for (int ch = 0; ch < 8; ++ch) {
+                    float v[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int gk = 64 * kb + 8 * ch + j;
+                        float x = 0.f;
+                        if (gi < N && gk < N) x = gi >= gk ? A[(size_t)gi + (size_t)gk * lda] : A[(size_t)gk + (size_t)gi * lda];
+                        v[j] = x;
+                    }
+                    sy_store_chunk(ah, al, t, ch, v);
+                }
+            } else {
+                const int sr = r % kSyRaw, ur = r / kSyRaw;
+                if (!mbar_wait(&raw_full[sr], ur & 1, err)) {
+                    s_fail = 1;
+                    break;
+                }
+                const float *rw = reinterpret_cast<const float *>(raw + sr * kSyRawBytes);
+                if (k == 0) {  // tile stored [k][i] (128 rows per k): thread t takes row t
+#pragma unroll 2
+                    for (int ch = 0; ch < 8; ++ch) {
+                        float v[8];
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) v[j] = rw[(8 * ch + j) * 128 + t];
+                        sy_store_chunk(ah, al, t, ch, v);
+                    }
+                } else {  // tile stored [i][k] (64 k per row): 8 threads per row, 16 rows per pass
+#pragma unroll 2
+                    for (int pass = 0; pass < 8; ++pass) {
+                        const int i = pass * 16 + (t >> 3), ch = t & 7;
+                        const float4 x0 = *reinterpret_cast<const float4 *>(rw + i * 64 + 8 * ch);
+                        const float4 x1 = *reinterpret_cast<const float4 *>(rw + i * 64 + 8 * ch + 4);
+                        const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+                        sy_store_chunk(ah, al, i, ch, v);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&raw_empty[sr]);
+                ++r;
+            }
+            fence_proxy_async_smem();  // the tensor core reads these tiles through the async proxy
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&a_full[sc]);
+        }
+    } else if (warp == 5 && lane == 0) {
+        // ---- MMA issuer
+        bool ok = true;
+        int c = 0;
+        for (int kb = kb0; kb < kb1; ++kb, ++c) {
+            const int sc = c % kSyCvt, uc = c / kSyCvt;
+            if (!mbar_wait(&u_full[sc], uc & 1, err) || !mbar_wait(&a_full[sc], uc & 1, err)) {
+                ok = false;
+                s_fail = 1;
+                break;
+            }
+            tc_fence_after();
+            unsigned char *cs = cvt + sc * kCvt;
+            const uint64_t dah = desc_sw128(cs), dal = desc_sw128(cs + 16384);
+            const uint64_t duh = desc_sw128(cs + 32768), dul = desc_sw128(cs + 32768 + BN * 128);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {  // K = 16 per instruction: +32 bytes = +2 in the address field
+                umma_bf16(tmem, dah + 2 * kk, duh + 2 * kk, kIdesc, (c | kk) != 0);
+                umma_bf16(tmem, dah + 2 * kk, dul + 2 * kk, kIdesc, 1);
+                umma_bf16(tmem, dal + 2 * kk, duh + 2 * kk, kIdesc, 1);
+            }
+            umma_commit(&cvt_empty[sc]);
+            s_mma_done = c + 1;
+        }
+        if (ok) umma_commit(&done);
+    }
+    __syncwarp();
+    // ---- epilogue: warps 1-4 read TMEM lanes 32 (warp mod 4) .. + 31
+    if (warp >= 1 && warp <= 4) {
+        const bool have = __all_sync(0xffffffffu, mbar_wait(&done, 0, err) ? 1 : 0) && !s_fail;
+        tc_fence_after();
+        if (have) {
+            const int quarter = warp & 3;
+            const int row = 128 * I + 32 * quarter + lane;
+            const uint32_t tb = tmem + ((uint32_t)(32 * quarter) << 16);
+            float *Y = Ypart + (size_t)s * split_stride;
+#pragma unroll 1
+            for (int cc = 0; cc < BN / 32; ++cc) {
+                float acc[32];
+                tmem_ld32(tb + cc * 32, acc);
+                if (row < N) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) Y[(size_t)row + (size_t)(cc * 32 + j) * N] = acc[j];
+                }
+            }
+        } else if (lane == 0) {
+            latch_error(err, SEV_ERR_TIMEOUT);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s_fail && threadIdx.x == 0) {
+        // a wait ran out: let the copies this CTA issued land and its MMAs
+        // finish before the TMEM is freed (the last phase of each stage)
+        const long long cap = kWaitCyclesDefault;
+        for (int q = 0; q < kSyRaw; ++q) {
+            int last = -1;
+            for (int r = 0; r < s_raw_issued; ++r)
+                if (r % kSyRaw == q) last = r;
+            if (last >= 0) mbar_wait_for(&raw_full[q], (last / kSyRaw) & 1, cap);
+        }
+        for (int q = 0; q < kSyCvt; ++q) {
+            int last = -1;
+            for (int c = 0; c < s_u_issued; ++c)
+                if (c % kSyCvt == q) last = c;
+            if (last >= 0) mbar_wait_for(&u_full[q], (last / kSyCvt) & 1, cap);
+        }
+        if (s_mma_done > 0) {
+            const int last = s_mma_done - 1;
+            mbar_wait_for(&cvt_empty[last % kSyCvt], (last / kSyCvt) & 1, cap);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, BN);
+}
+
+// U (N x b FP32, column-major, ld N) -> Uh, Ul (BF16, column-major, ld ldh).
+__global__ void split_u_kernel(int N, int b, int ldh, const float *__restrict__ U, __nv_bfloat16 *__restrict__ Uh,
+                               __nv_bfloat16 *__restrict__ Ul) {
+    const long total = (long)ldh * b;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        const int r = (int)(idx % ldh), c = (int)(idx / ldh);
+        const float u = r < N ? U[(size_t)r + (size_t)c * N] : 0.f;
+        const __nv_bfloat16 h = __float2bfloat16_rn(u);
+        Uh[idx] = h;
+        Ul[idx] = __float2bfloat16_rn(u - __bfloat162float(h));
+    }
+}
+
 // -------------------------------------------------------------- host side
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -323,6 +600,36 @@ static int make_map(CUtensorMap *m, void *base, int rows, int cols) {
     const cuuint32_t box[2] = {64, 128};
     const cuuint32_t es[2] = {1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SEV_OK : SEV_ERR_CUDA;
+}
+
+// 2D map of a column-major FP32 matrix (rows x cols, leading dimension ld
+// elements), boxes of box_r rows x box_c columns, no swizzle, zero fill.
+static int make_map_f32(CUtensorMap *m, const void *base, int rows, int cols, int ld, int box_r, int box_c) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return SEV_ERR_CUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)box_r, (cuuint32_t)box_c};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SEV_OK : SEV_ERR_CUDA;
+}
+
+// 2D map of a column-major BF16 matrix (rows x cols, ld elements, rows
+// contiguous), boxes of 64 rows x box_c columns, 128-byte swizzle.
+static int make_map_bf16_cm(CUtensorMap *m, const void *base, int rows, int cols, int ld, int box_c) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return SEV_ERR_CUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {64, (cuuint32_t)box_c};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? SEV_OK : SEV_ERR_CUDA;
@@ -376,11 +683,65 @@ int tc_syr2k(sev_ctx *h, int N, int b, T *A22, int lda, const T *U, const T *V, 
     }
 }
 
+template <typename T>
+int tc_symm_supported(sev_ctx *h, int N, int b, const T *A22, int lda) {
+    if (sizeof(T) != 4 || !tc_update_supported<T>(h, N, b)) return 0;
+    static int disabled = -1;
+    if (disabled < 0) disabled = getenv("SEV_NO_TC_SYMM") ? 1 : 0;
+    if (disabled) return 0;
+    return (b == 32 || b == 64 || b == 128) && N >= 256 && lda % 4 == 0 && ((uintptr_t)A22 & 15) == 0;
+}
+
+// Y = A22 U on the tensor cores; partial products of the K splits go to
+// ypart (kSymmMaxSplits x N x b) and are summed in split order into Y.
+template <typename T>
+int tc_symm(sev_ctx *h, int N, int b, const T *A22, int lda, const T *U, T *Y, T *ypart, int max_splits, void *ws) {
+    if constexpr (sizeof(T) != 4) {
+        return SEV_ERR_UNSUPPORTED;
+    } else {
+        const int ldh = (N + 7) / 8 * 8;
+        Carver c(ws);
+        __nv_bfloat16 *Uh = c.take<__nv_bfloat16>((size_t)ldh * b);
+        __nv_bfloat16 *Ul = c.take<__nv_bfloat16>((size_t)ldh * b);
+        int g = (int)(((long)ldh * b + 255) / 256);
+        if (g > h->sm_count * 16) g = h->sm_count * 16;
+        SEV_LAUNCH(h, K_SPLIT_BF16, split_u_kernel, g, 256, 0, N, b, ldh, U, Uh, Ul);
+        CUtensorMap mAc, mAr, mUh, mUl;
+        int rc = make_map_f32(&mAc, A22, N, N, lda, 128, 64);
+        if (!rc) rc = make_map_f32(&mAr, A22, N, N, lda, 64, 128);
+        if (!rc) rc = make_map_bf16_cm(&mUh, Uh, N, b, ldh, b);
+        if (!rc) rc = make_map_bf16_cm(&mUl, Ul, N, b, ldh, b);
+        if (rc) return rc;
+        const int nkb = (N + 63) / 64, rb = (N + 127) / 128;
+        // split K so that the grid covers about one wave of CTAs (one per SM)
+        int S = (h->sm_count + rb / 2) / rb;
+        S = S < 1 ? 1 : (S > max_splits ? max_splits : S);
+        const int per = (nkb + S - 1) / S;
+        S = (nkb + per - 1) / per;  // every split gets at least one K-block
+        const size_t smem = (size_t)kSyRaw * kSyRawBytes + (size_t)kSyCvt * sy_cvt_bytes(b) + 1024;
+        auto kern = b == 128 ? symm_tc_kernel<128> : (b == 64 ? symm_tc_kernel<64> : symm_tc_kernel<32>);
+        SEV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        float *dst = S > 1 ? (float *)ypart : (float *)Y;
+        SEV_LAUNCH(h, K_SYMM, kern, dim3(rb, S), kSyThreads, smem, mAc, mAr, mUh, mUl, (const float *)A22, lda, N, per,
+                   dst, (size_t)N * b, h->d_err);
+        if (S > 1) {
+            rc = launch_symm_reduce(h, N, b, S, (const float *)ypart, (float *)Y);
+            if (rc) return rc;
+        }
+        return SEV_OK;
+    }
+}
+
 template int tc_update_supported<float>(sev_ctx *, int, int);
 template int tc_update_supported<double>(sev_ctx *, int, int);
 template int tc_syr2k<float>(sev_ctx *, int, int, float *, int, const float *, const float *, void *);
 template int tc_syr2k<double>(sev_ctx *, int, int, double *, int, const double *, const double *, void *);
 template size_t tc_workspace<float>(int, int);
+template int tc_symm_supported<float>(sev_ctx *, int, int, const float *, int);
+template int tc_symm_supported<double>(sev_ctx *, int, int, const double *, int);
+template int tc_symm<float>(sev_ctx *, int, int, const float *, int, const float *, float *, float *, int, void *);
+template int tc_symm<double>(sev_ctx *, int, int, const double *, int, const double *, double *, double *, int,
+                             void *);
 template size_t tc_workspace<double>(int, int);
 
 }  // namespace sev
