@@ -159,12 +159,11 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         [&](int idx, T v) { Vs[idx] = v; });
     for (int k = threadIdx.x; k < nr; k += blockDim.x) taus[k] = tau[(size_t)node * b + k];
     const T *Zn = Zbuf + (size_t)node * b * b;
-    T m[Q][R];
-    unsigned qmask = 0;
+    T m[Q][R], cm[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int c = col0 + warp + kRegWarps * q;
-        if (c < b) qmask |= 1u << q;
+        cm[q] = c < b ? T(1) : T(0);
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             const int r = lane + 32 * t;
@@ -174,7 +173,7 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         }
     }
     __syncthreads();
-    reg_apply_all<T, R, Q>(m, Vs, 32 * R, taus, nr, (b % 32 == 0 && nc == 2) ? b : 0, qmask);
+    reg_apply_all<T, R, Q>(m, Vs, 32 * R, taus, nr, (b % 32 == 0 && nc == 2) ? b : 0, cm);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
@@ -209,12 +208,11 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         [&](int idx, T v) { Vs[idx] = v; });
     for (int k = threadIdx.x; k < nr; k += blockDim.x) taus[k] = tau[(size_t)l * b + k];
     const T *Zl = Zbuf + (size_t)l * b * b;
-    T m[Q][R];
-    unsigned qmask = 0;
+    T m[Q][R], cm[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int c = col0 + warp + kRegWarps * q;
-        if (c < b) qmask |= 1u << q;
+        cm[q] = c < b ? T(1) : T(0);
 #pragma unroll
         for (int t = 0; t < R; ++t) {
             const int r = lane + 32 * t;
@@ -222,7 +220,7 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         }
     }
     __syncthreads();
-    reg_apply_all<T, R, Q>(m, Vs, 32 * R, taus, nr, 0, qmask);
+    reg_apply_all<T, R, Q>(m, Vs, 32 * R, taus, nr, 0, cm);
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
@@ -452,22 +450,24 @@ static int reg_panel_run(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, c
         SEV_LAUNCH(h, K_TSQR_TREE, (rtsqr_node_qr_kernel<T, R, Q>), cnt[lev], kRegThreads, 0, b, cnt[lev - 1],
                    off[lev - 1], off[lev], B.Rbuf, Ylev, ystride, B.tau, B.nref);
     }
-    // the way down: slices of 16 x 4 columns per CTA
-    constexpr int QA = 4;
-    const int slices = (b + kRegWarps * QA - 1) / (kRegWarps * QA);
+    // the way down: the upper levels have few nodes, so 32-column slices
+    // (more CTAs); the leaves are many, so 64-column slices (V loaded fewer times)
+    constexpr int QN = 2, QL = 4;
+    const int slices_n = (b + kRegWarps * QN - 1) / (kRegWarps * QN);
+    const int slices_l = (b + kRegWarps * QL - 1) / (kRegWarps * QL);
     const size_t s_apply = sizeof(T) * ((size_t)32 * R * b + b);
-    SEV_CUDA(cudaFuncSetAttribute(rtsqr_node_apply_kernel<T, R, QA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SEV_CUDA(cudaFuncSetAttribute(rtsqr_node_apply_kernel<T, R, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)s_apply));
-    SEV_CUDA(cudaFuncSetAttribute(rtsqr_leaf_apply_kernel<T, R, QA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SEV_CUDA(cudaFuncSetAttribute(rtsqr_leaf_apply_kernel<T, R, QL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)s_apply));
     for (int lev = nlev - 1; lev >= 1; --lev) {
         T *Ylev = B.Ynode + (size_t)(off[lev] - L) * ystride;
-        SEV_LAUNCH(h, K_TSQR_DOWN, (rtsqr_node_apply_kernel<T, R, QA>), dim3(cnt[lev], slices), kRegThreads, s_apply,
-                   b, cnt[lev - 1], off[lev - 1], off[lev], Ylev, ystride, B.tau, B.nref, B.Zbuf,
+        SEV_LAUNCH(h, K_TSQR_DOWN, (rtsqr_node_apply_kernel<T, R, QN>), dim3(cnt[lev], slices_n), kRegThreads,
+                   s_apply, b, cnt[lev - 1], off[lev - 1], off[lev], Ylev, ystride, B.tau, B.nref, B.Zbuf,
                    lev == nlev - 1 ? 1 : 0);
     }
-    SEV_LAUNCH(h, K_TSQR_LEAF_Q, (rtsqr_leaf_apply_kernel<T, R, QA>), dim3(L, slices), kRegThreads, s_apply, N, b, L,
-               B.Yleaf, N, B.tau, B.nref, B.Zbuf, B.Q, N);
+    SEV_LAUNCH(h, K_TSQR_LEAF_Q, (rtsqr_leaf_apply_kernel<T, R, QL>), dim3(L, slices_l), kRegThreads, s_apply, N, b,
+               L, B.Yleaf, N, B.tau, B.nref, B.Zbuf, B.Q, N);
     const T *Rroot = B.Rbuf + (size_t)(off[nlev - 1]) * b * b;
     const size_t s_rec = sizeof(T) * (2 * (size_t)(b + 1) * b + 2 * 32 * RR + 2 * b);
     SEV_CUDA(cudaFuncSetAttribute(recon_reg_kernel<T, RR, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s_rec));

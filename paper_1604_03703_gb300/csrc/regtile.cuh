@@ -33,46 +33,79 @@ __device__ __forceinline__ T rsel(const T (&x)[R], int t) {
     return r;
 }
 
-// Does the 32-row block t hold a row where reflector k can be nonzero?
-// bstack = 0: dense (rows >= k); bstack = b (a multiple of 32): a stack of
-// upper triangles of height b (row k of the first, rows 0..k of the others).
-__device__ __forceinline__ bool rblk_active(int t, int k, int bstack) {
-    const int r0 = 32 * t;
-    if (bstack == 0) return r0 + 31 >= k;
-    if (r0 <= k && k < r0 + 32) return true;
-    return r0 >= bstack && (r0 % bstack) <= k;
-}
-
-// Columns q of `a` in qmask (warp-uniform) <- H a, H = I - tau v v^T, v given
-// per lane row in vr (zero outside the active blocks).  The dot products of
-// all selected columns are reduced together so their shuffle chains overlap.
-template <typename T, int R, int Q>
-__device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const bool (&act)[R], T tau,
-                                          unsigned qmask) {
-    T d[Q];
+// The 32-row blocks of the tile that can hold a nonzero of reflector k.
+// bstack = 0: a dense block (reflector k lives in rows >= k); bstack = b (a
+// multiple of 32): a stack of upper triangles of height b, where reflector k
+// is nonzero only in row k of the first triangle and rows 0..k of the others.
+// The block offsets are formed once, so the per-step test is a comparison.
+template <int R>
+struct RowBlocks {
+    int toff[R];    // offset of block t's first row inside its triangle
+    bool lower[R];  // block t lies in a triangle below the first
+    int bstack;
+    __device__ __forceinline__ explicit RowBlocks(int bs) : bstack(bs) {
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        d[q] = T(0);
-        if ((qmask >> q) & 1u) {
-#pragma unroll
-            for (int t = 0; t < R; ++t)
-                if (act[t]) d[q] = fmat(vr[t], a[q][t], d[q]);
+        for (int t = 0; t < R; ++t) {
+            lower[t] = bs > 0 && 32 * t >= bs;
+            toff[t] = bs > 0 ? (32 * t) % bs : 32 * t;
         }
     }
+    __device__ __forceinline__ bool active(int t, int k) const {
+        if (bstack == 0) return 32 * t + 31 >= k;
+        return lower[t] ? toff[t] <= k : (32 * t <= k && k < 32 * t + 32);
+    }
+};
+
+// a <- H a on every column, H = I - tau v v^T, v given per lane row in vr
+// (zero outside the active blocks), each column's update scaled by cm[q]
+// (1: apply, 0: leave the column exactly as it is).  The branches are on
+// the warp-uniform row blocks only; the dot products of all columns are
+// reduced together so their shuffle chains overlap.
+template <typename T, int R, int Q>
+__device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const bool (&act)[R], T tau,
+                                          const T (&cm)[Q]) {
+    T d[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) d[q] = T(0);
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+        if (act[t]) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) d[q] = fmat(vr[t], a[q][t], d[q]);
+        }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < Q; ++q)
-            if ((qmask >> q) & 1u) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+        for (int q = 0; q < Q; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+    T sc[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
-        if ((qmask >> q) & 1u) {
-            const T s = tau * d[q];
+    for (int q = 0; q < Q; ++q) sc[q] = tau * d[q] * cm[q];
 #pragma unroll
-            for (int t = 0; t < R; ++t)
-                if (act[t]) a[q][t] = fmat(-s, vr[t], a[q][t]);
+    for (int t = 0; t < R; ++t)
+        if (act[t]) {
+#pragma unroll
+            for (int q = 0; q < Q; ++q) a[q][t] = fmat(-sc[q], vr[t], a[q][t]);
         }
-    }
+}
+
+// x <- column q of a / column q of a <- x (q warp-uniform; one branch taken).
+template <typename T, int R, int Q>
+__device__ __forceinline__ void reg_col_get(const T (&a)[Q][R], int q, T (&x)[R]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (i == q) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) x[t] = a[i][t];
+        }
+}
+template <typename T, int R, int Q>
+__device__ __forceinline__ void reg_col_put(T (&a)[Q][R], int q, const T (&x)[R]) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+        if (i == q) {
+#pragma unroll
+            for (int t = 0; t < R; ++t) a[i][t] = x[t];
+        }
 }
 
 // Reflector of rows k..m-1 of the column x (one warp; lane rows lane + 32 t;
@@ -174,6 +207,7 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
         __syncthreads();
         return 0;
     }
+    const RowBlocks<R> blk(bstack);
     if (warp == 0) {
         const T t0 = reg_house<T, R>(a[0], 0, vs);
         if (lane == 0) taus[0] = t0;
@@ -186,51 +220,48 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
         T vr[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            act[t] = rblk_active(t, k, bstack);
+            act[t] = blk.active(t, k);
             vr[t] = act[t] ? v[lane + 32 * t] : T(0);
         }
-        unsigned mine = 0;
+        T cm[Q];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int c = warp + NW * q;
-            if (c > k && c < nc) mine |= 1u << q;
+            cm[q] = (c > k && c < nc) ? T(1) : T(0);
         }
         const int k1 = k + 1;
         if (k1 < nc && (k1 % NW) == warp) {
-            // lookahead: column k+1 first (copied out of the tile, so the
+            // lookahead: column k+1 first (taken out of the tile, so the
             // reflector code is emitted once), then reflector k+1 from it
             const int q1 = k1 / NW;
             T x[1][R];
-#pragma unroll
-            for (int t = 0; t < R; ++t) x[0][t] = a[0][t];
-#pragma unroll
-            for (int q = 1; q < Q; ++q)
-#pragma unroll
-                for (int t = 0; t < R; ++t)
-                    if (q == q1) x[0][t] = a[q][t];
-            if (tk != T(0)) reg_apply<T, R, 1>(x, vr, act, tk, 1u);
+            reg_col_get<T, R, Q>(a, q1, x[0]);
+            if (tk != T(0)) {
+                const T one[1] = {T(1)};
+                reg_apply<T, R, 1>(x, vr, act, tk, one);
+            }
             if (k1 < r) {
                 const T t1 = reg_house<T, R>(x[0], k1, vs + (k1 & 1) * (32 * R));
                 if (lane == 0) taus[k1] = t1;
             }
+            reg_col_put<T, R, Q>(a, q1, x[0]);
 #pragma unroll
             for (int q = 0; q < Q; ++q)
-#pragma unroll
-                for (int t = 0; t < R; ++t)
-                    if (q == q1) a[q][t] = x[0][t];
-            mine &= ~(1u << q1);
+                if (q == q1) cm[q] = T(0);
         }
-        if (tk != T(0) && mine) reg_apply<T, R, Q>(a, vr, act, tk, mine);
+        if (tk != T(0)) reg_apply<T, R, Q>(a, vr, act, tk, cm);
         __syncthreads();
     }
     return r;
 }
 
 // M <- H_0 H_1 ... H_{nr-1} M: reflectors explicit in Vs (column k at
-// Vs[k * ldv], rows 0 .. 32R), scalars in taus; columns of M in qmask.
+// Vs[k * ldv], rows 0 .. 32R), scalars in taus; columns of M with cm[q] = 1.
 template <typename T, int R, int Q>
-__device__ void reg_apply_all(T (&m)[Q][R], const T *Vs, int ldv, const T *taus, int nr, int bstack, unsigned qmask) {
+__device__ void reg_apply_all(T (&m)[Q][R], const T *Vs, int ldv, const T *taus, int nr, int bstack,
+                              const T (&cm)[Q]) {
     const int lane = threadIdx.x & 31;
+    const RowBlocks<R> blk(bstack);
     for (int k = nr - 1; k >= 0; --k) {
         const T tk = taus[k];
         if (tk == T(0)) continue;
@@ -238,10 +269,10 @@ __device__ void reg_apply_all(T (&m)[Q][R], const T *Vs, int ldv, const T *taus,
         T vr[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            act[t] = rblk_active(t, k, bstack);
+            act[t] = blk.active(t, k);
             vr[t] = act[t] ? Vs[(size_t)k * ldv + lane + 32 * t] : T(0);
         }
-        reg_apply<T, R, Q>(m, vr, act, tk, qmask);
+        reg_apply<T, R, Q>(m, vr, act, tk, cm);
     }
 }
 

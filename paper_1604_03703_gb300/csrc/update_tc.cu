@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(128, 1)
 // Y = A22 U, the first product of the V formation (W = A22 U in Eq. 4.1 /
 // Algorithm 4.1), for FP32 data on the tensor cores in BF16x3:
 // Y ~ Ah Uh + Ah Ul + Al Uh (hi/lo splits as in split_bf16x3_kernel; the
-// Al Ul term, ~2^-16 relative, dropped), FP32 accumulation in TMEM.
+// Al Ul term, ~2^-16 relative, dropped).
 //
 // CTA (I, s) computes rows [128 I, 128 I + 128) of Y over the 64-wide
 // K-blocks of split s.  A22 is stored in its lower triangle only, so the A
@@ -310,13 +310,23 @@ __global__ void __launch_bounds__(128, 1)
 // tile into BF16 hi and lo tiles in the K-major, 128-byte-swizzled layout
 // of the MMA operand (16-byte chunk c of row i at chunk c ^ (i mod 8)); the
 // U tiles, split once per panel, arrive by TMA in that layout.
-// Warps: 0 TMA producer, 1-4 converters and epilogue, 5 MMA issuer.  Every
-// wait is time-capped; a CTA whose wait runs out latches SEV_ERR_TIMEOUT,
-// lets the copies and MMAs it issued finish, frees its TMEM and returns.
+//
+// Accumulation.  The tensor core sums at most kSyChunk K-blocks (512 terms)
+// in TMEM; the chunks alternate between two TMEM accumulators, and four
+// accumulator warps add each finished chunk into an FP32 register sum (IEEE
+// round-to-nearest) while the next chunk is being multiplied.  Summing all
+// N terms in TMEM made the error grow with N (measured: 5.8e-5 ||A|| at
+// n = 16384 against 3.7e-6 at n = 4096).
+//
+// Warps: 0 TMA producer, 1-4 converters, 5 MMA issuer, 6-9 accumulators
+// (TMEM lanes 32 (warp mod 4) .. + 31, i.e. tile rows).  Every wait is
+// time-capped; a CTA whose wait runs out latches SEV_ERR_TIMEOUT, lets the
+// copies and MMAs it issued finish, frees its TMEM and returns.
 constexpr int kSyRaw = 2;                   // FP32 tile stages
 constexpr int kSyCvt = 2;                   // converted operand stages
 constexpr int kSyRawBytes = 128 * 64 * 4;   // one FP32 tile
-constexpr int kSyThreads = 192;
+constexpr int kSyChunk = 8;                 // K-blocks summed in TMEM before the register sum
+constexpr int kSyThreads = 320;
 __host__ __device__ constexpr int sy_cvt_bytes(int bn) { return 2 * 128 * 128 + 2 * bn * 128; }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
@@ -356,13 +366,14 @@ __global__ void __launch_bounds__(kSyThreads, 1)
     unsigned char *raw = smem;
     unsigned char *cvt = raw + kSyRaw * kSyRawBytes;
     __shared__ __align__(8) uint64_t raw_full[kSyRaw], raw_empty[kSyRaw], u_full[kSyCvt], a_full[kSyCvt],
-        cvt_empty[kSyCvt], done;
+        cvt_empty[kSyCvt], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int s_fail, s_raw_issued, s_u_issued, s_mma_done;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int I = blockIdx.x, s = blockIdx.y;
     const int nkb = (N + 63) / 64;
     const int kb0 = s * kb_per_split, kb1 = min(nkb, kb0 + kb_per_split);
+    const int nblk = kb1 - kb0, nchunk = (nblk + kSyChunk - 1) / kSyChunk;
     // 0: below the diagonal block, 1: above it, 2: meets the diagonal
     auto kind = [&](int kb) { return 64 * kb + 64 <= 128 * I ? 0 : (64 * kb >= 128 * I + 128 ? 1 : 2); };
 
@@ -376,7 +387,10 @@ __global__ void __launch_bounds__(kSyThreads, 1)
             mbar_init(&a_full[q], 4);
             mbar_init(&cvt_empty[q], 1);
         }
-        mbar_init(&done, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&acc_full[q], 1);
+            mbar_init(&acc_empty[q], 4);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_fail = 0;
         s_raw_issued = 0;
@@ -384,7 +398,7 @@ __global__ void __launch_bounds__(kSyThreads, 1)
         s_mma_done = 0;
     }
     if (warp == 0) {
-        tmem_alloc(&tmem_base, BN);
+        tmem_alloc(&tmem_base, 2 * BN);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -482,13 +496,17 @@ __global__ void __launch_bounds__(kSyThreads, 1)
             if (lane == 0) mbar_arrive(&a_full[sc]);
         }
     } else if (warp == 5 && lane == 0) {
-        // ---- MMA issuer
-        bool ok = true;
+        // ---- MMA issuer: chunk ch of kSyChunk K-blocks into TMEM buffer ch & 1
         int c = 0;
         for (int kb = kb0; kb < kb1; ++kb, ++c) {
+            const int ch = c / kSyChunk, buf = ch & 1;
+            const bool first = c % kSyChunk == 0, last = c % kSyChunk == kSyChunk - 1 || kb + 1 == kb1;
+            if (first && ch >= 2 && !mbar_wait(&acc_empty[buf], ((ch >> 1) - 1) & 1, err)) {
+                s_fail = 1;
+                break;
+            }
             const int sc = c % kSyCvt, uc = c / kSyCvt;
             if (!mbar_wait(&u_full[sc], uc & 1, err) || !mbar_wait(&a_full[sc], uc & 1, err)) {
-                ok = false;
                 s_fail = 1;
                 break;
             }
@@ -496,35 +514,49 @@ __global__ void __launch_bounds__(kSyThreads, 1)
             unsigned char *cs = cvt + sc * kCvt;
             const uint64_t dah = desc_sw128(cs), dal = desc_sw128(cs + 16384);
             const uint64_t duh = desc_sw128(cs + 32768), dul = desc_sw128(cs + 32768 + BN * 128);
+            const uint32_t dt = tmem + (uint32_t)(buf * BN);
 #pragma unroll
             for (int kk = 0; kk < 4; ++kk) {  // K = 16 per instruction: +32 bytes = +2 in the address field
-                umma_bf16(tmem, dah + 2 * kk, duh + 2 * kk, kIdesc, (c | kk) != 0);
-                umma_bf16(tmem, dah + 2 * kk, dul + 2 * kk, kIdesc, 1);
-                umma_bf16(tmem, dal + 2 * kk, duh + 2 * kk, kIdesc, 1);
+                umma_bf16(dt, dah + 2 * kk, duh + 2 * kk, kIdesc, (first && kk == 0) ? 0u : 1u);
+                umma_bf16(dt, dah + 2 * kk, dul + 2 * kk, kIdesc, 1);
+                umma_bf16(dt, dal + 2 * kk, duh + 2 * kk, kIdesc, 1);
             }
             umma_commit(&cvt_empty[sc]);
+            if (last) umma_commit(&acc_full[buf]);
             s_mma_done = c + 1;
         }
-        if (ok) umma_commit(&done);
-    }
-    __syncwarp();
-    // ---- epilogue: warps 1-4 read TMEM lanes 32 (warp mod 4) .. + 31
-    if (warp >= 1 && warp <= 4) {
-        const bool have = __all_sync(0xffffffffu, mbar_wait(&done, 0, err) ? 1 : 0) && !s_fail;
-        tc_fence_after();
-        if (have) {
-            const int quarter = warp & 3;
-            const int row = 128 * I + 32 * quarter + lane;
-            const uint32_t tb = tmem + ((uint32_t)(32 * quarter) << 16);
-            float *Y = Ypart + (size_t)s * split_stride;
-#pragma unroll 1
+    } else if (warp >= 6) {
+        // ---- accumulators: register sum of the chunks, then the rows of Y
+        const int quarter = warp & 3;
+        const uint32_t tb = tmem + ((uint32_t)(32 * quarter) << 16);
+        float sum[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) sum[j] = 0.f;
+        bool ok = true;
+        for (int ch = 0; ch < nchunk; ++ch) {
+            const int buf = ch & 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (ch >> 1) & 1, err) ? 1 : 0)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
             for (int cc = 0; cc < BN / 32; ++cc) {
                 float acc[32];
-                tmem_ld32(tb + cc * 32, acc);
-                if (row < N) {
+                tmem_ld32(tb + (uint32_t)(buf * BN + cc * 32), acc);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) Y[(size_t)row + (size_t)(cc * 32 + j) * N] = acc[j];
-                }
+                for (int j = 0; j < 32; ++j) sum[cc * 32 + j] += acc[j];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+        if (ok && !s_fail) {
+            const int row = 128 * I + 32 * quarter + lane;
+            float *Y = Ypart + (size_t)s * split_stride;
+            if (row < N) {
+#pragma unroll
+                for (int j = 0; j < BN; ++j) Y[(size_t)row + (size_t)j * N] = sum[j];
             }
         } else if (lane == 0) {
             latch_error(err, SEV_ERR_TIMEOUT);
@@ -555,7 +587,7 @@ __global__ void __launch_bounds__(kSyThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, BN);
+    if (warp == 0) tmem_dealloc(tmem, 2 * BN);
 }
 
 // U (N x b FP32, column-major, ld N) -> Uh, Ul (BF16, column-major, ld ldh).
