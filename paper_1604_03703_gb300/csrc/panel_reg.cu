@@ -281,18 +281,17 @@ __global__ void __launch_bounds__(kRegThreads, 1)
                 }
         }
         __syncthreads();
+        // rows <= k have l = 0 and columns <= k a zero scale: every update is
+        // an unconditional FMA (x - 0 * u leaves x unchanged)
         T lr[R];
 #pragma unroll
         for (int t = 0; t < R; ++t) lr[t] = l[lane + 32 * t];
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
             const int c = warp + kRegWarps * q;
-            if (c > k && c < b) {
-                const T u = __shfl_sync(0xffffffffu, rsel<R>(m[q], k >> 5), k & 31);
+            const T u = __shfl_sync(0xffffffffu, rsel<R>(m[q], k >> 5), k & 31) * ((c > k && c < b) ? T(1) : T(0));
 #pragma unroll
-                for (int t = 0; t < R; ++t)
-                    if (lane + 32 * t > k) m[q][t] = fmat(-lr[t], u, m[q][t]);
-            }
+            for (int t = 0; t < R; ++t) m[q][t] = fmat(-lr[t], u, m[q][t]);
         }
     }
     __syncthreads();
@@ -334,21 +333,19 @@ __global__ void __launch_bounds__(kRegThreads, 1)
                 }
         }
         __syncthreads();
-        const T dq = dg[qq];
+        const T rdq = T(1) / dg[qq];
         T wr[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) wr[t] = w[lane + 32 * t];
+        for (int t = 0; t < R; ++t) wr[t] = w[lane + 32 * t];  // 0 on rows >= qq
+        const int tq = qq >> 5;
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int c = warp + kRegWarps * q;
-            if (c >= qq && c < b) {
-                const T xq = __shfl_sync(0xffffffffu, rsel<R>(x[q], qq >> 5), qq & 31) / dq;
+            // columns c < qq have x[qq, c] = 0 and stay unchanged; row qq is scaled
+            const T xq = __shfl_sync(0xffffffffu, rsel<R>(x[q], tq), qq & 31) * rdq;
 #pragma unroll
-                for (int t = 0; t < R; ++t) {
-                    const int row = lane + 32 * t;
-                    if (row == qq) x[q][t] = xq;
-                    if (row < qq) x[q][t] = fmat(-wr[t], xq, x[q][t]);
-                }
+            for (int t = 0; t < R; ++t) {
+                x[q][t] = fmat(-wr[t], xq, x[q][t]);
+                if (t == tq && lane == (qq & 31)) x[q][t] = xq;
             }
         }
     }
@@ -383,16 +380,13 @@ __global__ void __launch_bounds__(kRegThreads, 1)
         __syncthreads();
         T lr[R];
 #pragma unroll
-        for (int t = 0; t < R; ++t) lr[t] = l[lane + 32 * t];
+        for (int t = 0; t < R; ++t) lr[t] = l[lane + 32 * t];  // 0 on rows <= qq
 #pragma unroll
         for (int q = 0; q < Q; ++q) {
-            const int c = warp + kRegWarps * q;
-            if (c <= qq) {
-                const T yq = __shfl_sync(0xffffffffu, rsel<R>(x[q], qq >> 5), qq & 31);
+            // columns c > qq have y[qq, c] = 0: the update leaves them unchanged
+            const T yq = __shfl_sync(0xffffffffu, rsel<R>(x[q], qq >> 5), qq & 31);
 #pragma unroll
-                for (int t = 0; t < R; ++t)
-                    if (lane + 32 * t > qq) x[q][t] = fmat(-lr[t], yq, x[q][t]);
-            }
+            for (int t = 0; t < R; ++t) x[q][t] = fmat(-lr[t], yq, x[q][t]);
         }
     }
 #pragma unroll
