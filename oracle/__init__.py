@@ -116,6 +116,10 @@ def _load():
             lib.orc_band_inertia.argtypes = [i, _dp, i, i, d]
             lib.orc_panel_qr.restype = i
             lib.orc_panel_qr.argtypes = [i, i, _dp, i, _dp, i, _dp, i]
+            lib.orc_sign_margin_reset.restype = None
+            lib.orc_sign_margin_reset.argtypes = []
+            lib.orc_sign_margin_get.restype = d
+            lib.orc_sign_margin_get.argtypes = []
             lib.orc_full_to_band.restype = None
             lib.orc_full_to_band.argtypes = [i, _dp, i, i]
             lib.orc_band_to_band.restype = None
@@ -311,13 +315,17 @@ def panel_qr(P):
     return P, U[:, :r], T[:r, :r], r
 
 
-def full_to_band(A, b: int):
-    """Algorithm 4.1 (right-looking): returns the full symmetric band matrix."""
+def full_to_band(A, b: int, return_margin: bool = False):
+    """Algorithm 4.1 (right-looking): returns the full symmetric band matrix
+    (and, with return_margin, the smallest |alpha|/||x|| of its reflectors:
+    the band is unique entry by entry when that is far above rounding)."""
     M = _fortran(A)
     M = np.tril(M) + np.tril(M, -1).T  # full symmetric storage from the lower triangle
     M = np.asfortranarray(M)
-    _load().orc_full_to_band(M.shape[0], _ptr(M), M.shape[0], int(b))
-    return M
+    lib = _load()
+    lib.orc_sign_margin_reset()
+    lib.orc_full_to_band(M.shape[0], _ptr(M), M.shape[0], int(b))
+    return (M, lib.orc_sign_margin_get()) if return_margin else M
 
 
 def band_to_band(B, b: int, h: int, nc_paper: bool = False, max_chases: int = -1):

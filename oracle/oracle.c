@@ -606,6 +606,19 @@ int orc_band_inertia(int n, const double *AB, int ldab, int b, double x)
  * the forward recurrence T[0:k,k] = -tau_k T[0:k,0:k] U[:,0:k]^T U[:,k]
  * (Cor. 3.7's Householder representation).  Returns r.
  */
+/*
+ * Sign margin of the Householder reflectors formed since the last reset:
+ * the smallest |alpha| / ||x|| (alpha the leading entry before reflection).
+ * The "always reflect" rule takes beta's sign from alpha, so a reduction
+ * whose margin is far above the working precision's rounding error makes
+ * the same sign choices in any precision -- the condition under which the
+ * band produced by full_to_band is unique entry by entry.  Reporting only;
+ * it changes no arithmetic.
+ */
+static double g_sign_margin = 1.0;
+void orc_sign_margin_reset(void) { g_sign_margin = 1.0; }
+double orc_sign_margin_get(void) { return g_sign_margin; }
+
 int orc_panel_qr(int m, int nc, double *P, int ldp, double *U, int ldu, double *T, int ldt)
 {
     int r = nc < m - 1 ? nc : m - 1;
@@ -615,7 +628,9 @@ int orc_panel_qr(int m, int nc, double *P, int ldp, double *U, int ldu, double *
     for (int k = 0; k < r; ++k) {
         double beta;
         double *x = &P[IDX(k, k, ldp)];
+        double alpha = x[0];
         double t = orc_house(m - k, x, 1, &beta);
+        if (beta != 0.0 && fabs(alpha) / fabs(beta) < g_sign_margin) g_sign_margin = fabs(alpha) / fabs(beta);
         tau[k] = t;
         /* store v in U (unit lower trapezoidal) */
         for (int i = 0; i < m; ++i) U[IDX(i, k, ldu)] = (i < k) ? 0.0 : (i == k ? 1.0 : x[i - k]);

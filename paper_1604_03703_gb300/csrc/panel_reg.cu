@@ -32,6 +32,12 @@
 // column broadcast through shared memory and the pivot row through a shuffle.
 #include "regtile.cuh"
 
+#ifdef SEV_TRACE
+extern "C" int sev_trace_set_reg(void *p) {
+    return cudaMemcpyToSymbol(sev_rtrace, &p, sizeof(p)) == cudaSuccess ? 0 : 1;
+}
+#endif
+
 namespace sev {
 
 constexpr int kRegWarps = 16;

@@ -10,6 +10,20 @@
 
 #include "common.cuh"
 
+#ifdef SEV_TRACE
+// per-step clocks of reg_qr in CTA 0 (trace builds only; set by the host)
+static __device__ long long *sev_rtrace = nullptr;
+#define RTRACE(k, slot)                                                                       \
+    do {                                                                                      \
+        if (sev_rtrace && blockIdx.x == 0 && blockIdx.y == 0 && (threadIdx.x & 31) == 0 && (k) < 256) \
+            sev_rtrace[(k) * 4 + (slot)] = clock64();                                         \
+    } while (0)
+#else
+#define RTRACE(k, slot) \
+    do {                \
+    } while (0)
+#endif
+
 namespace sev {
 
 template <typename T>
@@ -230,6 +244,7 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
             cm[q] = (c > k && c < nc) ? T(1) : T(0);
         }
         const int k1 = k + 1;
+        if (warp == 0) RTRACE(k, 0);
         if (k1 < nc && (k1 % NW) == warp) {
             // lookahead: column k+1 first (taken out of the tile, so the
             // reflector code is emitted once), then reflector k+1 from it
@@ -240,16 +255,19 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
                 const T one[1] = {T(1)};
                 reg_apply<T, R, 1>(x, vr, act, tk, one);
             }
+            RTRACE(k, 1);
             if (k1 < r) {
                 const T t1 = reg_house<T, R>(x[0], k1, vs + (k1 & 1) * (32 * R));
                 if (lane == 0) taus[k1] = t1;
             }
+            RTRACE(k, 2);
             reg_col_put<T, R, Q>(a, q1, x[0]);
 #pragma unroll
             for (int q = 0; q < Q; ++q)
                 if (q == q1) cm[q] = T(0);
         }
         if (tk != T(0)) reg_apply<T, R, Q>(a, vr, act, tk, cm);
+        if (k1 < nc && (k1 % NW) == warp) RTRACE(k, 3);
         __syncthreads();
     }
     return r;
