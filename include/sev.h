@@ -236,6 +236,39 @@ int sev_batch_autotune(sev_handle handle, int count, const int *n, int prec, int
  */
 int sev_band_schedule(int n, int b0, int prec, int *bands, int max_bands);
 
+/*
+ * Autotuner of the band widths sev_eigvalsh goes through (Algorithm 4.3
+ * reduces to a first half-bandwidth b0, then through narrower bands to the
+ * tridiagonal; the paper fixes neither b0 nor the stage widths for a
+ * machine, and Algorithm 4.2 holds for any h dividing b).  On this handle's
+ * GPU, at the order n and precision prec, it times once each: the
+ * full-to-band reduction for every candidate b0 (32, 64 and 128 when
+ * b0 = 0; only b0 otherwise -- a power of two up to 128), and every band
+ * stage b -> h (powers of two, h | b) the kernels support; the cheapest
+ * stage path from each width down to 1 follows by dynamic programming over
+ * the measured costs.  The result is kept in the handle for the bucket of
+ * n (orders within a factor sqrt 2) and prec: later sev_eigvalsh calls in
+ * that bucket run the tuned stage path from their b0, and calls with
+ * b0 = 0 take the tuned b0 (tuned only when this call had b0 = 0).  With
+ * the environment variable SEV_TUNE_CACHE naming a file, the result is also
+ * appended there, keyed by the GPU's name, and read back by sev_create.
+ *   bands      host, receives the widths from b0 (b0 as given, or the tuned
+ *              one) down to 1; max_bands entries available
+ *   best_ms    host, may be NULL: the predicted milliseconds of the
+ *              reductions (full-to-band plus band stages) along that path
+ * Returns the number of widths written (0 for n < 4), -i for invalid
+ * argument i, or an SEV_ERR_* code.  Allocates an n x n test matrix and
+ * the workspace, and synchronises the handle's stream.
+ */
+int sev_autotune(sev_handle handle, int n, int prec, int b0, int *bands, int max_bands, double *best_ms);
+
+/* The band widths sev_eigvalsh(handle, n, ., ., b0, prec, .) runs (host
+ * only, no device work): as sev_band_schedule, but with this handle's
+ * autotuned b0 and stage widths where sev_autotune set them.  Returns the
+ * number of widths, -6 if max_bands is too small, or -i for invalid
+ * argument i. */
+int sev_eigvalsh_bands(sev_handle handle, int n, int b0, int prec, int *bands, int max_bands);
+
 /* Copy the diagonal and first subdiagonal of a packed band (float or double
  * by prec) into FP64 device arrays d (n) and e (n-1). */
 int sev_band_tridiag_extract(sev_handle handle, int n, const void *AB, int ldab, int prec, double *d,

@@ -173,6 +173,25 @@ class Handle:
         check(self._lib.sev_batch_autotune(self._h, len(sizes), arr, prec, ctypes.byref(best)), "sev_batch_autotune")
         return best.value
 
+    def autotune(self, n: int, prec: int, b0: int = 0):
+        """Tune the band widths of eigvalsh at order n (sev_autotune): returns
+        (widths from b0 down to 1, predicted reduction milliseconds)."""
+        self._sync_stream()
+        bands = (ctypes.c_int * 16)()
+        ms = ctypes.c_double()
+        k = self._lib.sev_autotune(self._h, int(n), int(prec), int(b0), bands, 16, ctypes.byref(ms))
+        if k < 0 or k > 16:
+            check(k if k < 0 else -6, "sev_autotune")
+        return list(bands[:k]), ms.value
+
+    def eigvalsh_bands(self, n: int, b0: int, prec: int):
+        """The band widths eigvalsh(n, b0, prec) runs on this handle."""
+        bands = (ctypes.c_int * 40)()
+        k = self._lib.sev_eigvalsh_bands(self._h, int(n), int(b0), int(prec), bands, 40)
+        if k < 0:
+            check(k, "sev_eigvalsh_bands")
+        return list(bands[:k])
+
     def get_error(self) -> int:
         return self._lib.sev_get_error(self._h)
 

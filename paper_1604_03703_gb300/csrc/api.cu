@@ -95,6 +95,13 @@ static int default_b0(int n, int prec) {
     return n >= 1024 ? 64 : 32;  // 64 -> 16 -> 1 measured best at n = 16384 (1.18 s against 1.51 s for 128)
 }
 
+// b0 for a call with b0 = 0: the autotuned width of the order's bucket if
+// sev_autotune chose one on this handle, else the default rule.
+static int pick_b0(const sev_ctx *h, int n, int prec) {
+    const TunedBands *t = tuned_for(h, n, prec);
+    return (t && t->b0 > 0) ? t->b0 : default_b0(n, prec);
+}
+
 // Band schedule (Algorithm 4.3; the paper allows a reduction factor k > 2
 // per stage).  Measured on GB300 at n = 16384 (FP32): the one-stage b -> 1
 // kernel is fastest from b = 16 (192 ms, against 366 ms from 32), a
@@ -136,10 +143,20 @@ static int band_stage(sev_ctx *h, int n, T *AB, int ldab, int b, int hh, void *w
     return launch_band_to_band<T>(h, n, AB, ldab, b, hh, ws, ws_bytes);
 }
 
+// The stage widths sev_eigvalsh runs from b0: the autotuned table of the
+// order's bucket when it reaches 1 from b0, else schedule().
+static int stages_for(const sev_ctx *h, int n, int b0, int prec, int *out) {
+    if (const TunedBands *t = tuned_for(h, n, prec)) {
+        const int k = tuned_schedule(*t, b0, out, 40);
+        if (k > 0) return k;
+    }
+    return schedule(b0, prec == SEV_FP64 ? 8 : 4, out);
+}
+
 template <typename T>
 static size_t eig_workspace(sev_ctx *h, int n, int b0) {
     int sched[40];
-    const int ns = schedule(b0, (int)sizeof(T), sched);
+    const int ns = stages_for(h, n, b0, sizeof(T) == 8 ? SEV_FP64 : SEV_MIXED, sched);
     const int ldab = 2 * b0 > 2 ? 2 * b0 : 2;
     size_t stage = bisect_workspace(n);
     if (b0 < n - 1) {
@@ -164,7 +181,7 @@ template <typename T>
 static int eigvalsh_t(sev_ctx *h, int n, T *A, int lda, int b0, double *eigs) {
     if (b0 > n - 1) b0 = n - 1 > 1 ? n - 1 : 1;
     int sched[40];
-    const int ns = schedule(b0, (int)sizeof(T), sched);
+    const int ns = stages_for(h, n, b0, sizeof(T) == 8 ? SEV_FP64 : SEV_MIXED, sched);
     for (int s = 0; s + 1 < ns; ++s)
         if (!(sched[s + 1] == 1 && band_tri_supported(sched[s], (int)sizeof(T))) &&
             band_smem_bytes<T>(sched[s], sched[s + 1]) > h->smem_optin)
@@ -280,6 +297,7 @@ int sev_create(sev_handle *handle, int device) {
         return SEV_ERR_CUDA;
     }
     if (const char *v = getenv("SEV_LEAF_ROWS")) h->leaf_rows_override = atoi(v);
+    tune_cache_load(h);
     *handle = h;
     return SEV_OK;
 }
@@ -314,7 +332,7 @@ int sev_workspace_query(sev_handle h, int n, int b0, int prec, size_t *bytes) {
         *bytes = 0;
         return SEV_OK;
     }
-    if (b0 == 0) b0 = default_b0(n, prec);
+    if (b0 == 0) b0 = pick_b0(h, n, prec);
     if (b0 > n - 1) b0 = n - 1 > 1 ? n - 1 : 1;
     *bytes = prec == SEV_FP64 ? eig_workspace<double>(h, n, b0) : eig_workspace<float>(h, n, b0);
     return SEV_OK;
@@ -338,7 +356,7 @@ int sev_eigvalsh(sev_handle h, int n, void *A, int lda, int b0, int prec, double
     if (n > 0 && !eigs) return -7;
     if (n == 0) return SEV_OK;
     if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
-    if (b0 == 0) b0 = default_b0(n, prec);
+    if (b0 == 0) b0 = pick_b0(h, n, prec);
     if (n == 1) {
         // a 1 x 1 matrix: its entry is the eigenvalue
         const int rc = prec == SEV_FP64 ? launch_check_finite<double>(h, 1, (const double *)A, lda, nullptr)
@@ -527,7 +545,7 @@ int sev_batch_plan_create(sev_handle h, int count, const int *n, const int *lda,
     // reserve the single-matrix workspace now, so that running the plan allocates nothing
     size_t need = 0;
     for (const auto &g : P->big) {
-        const int b0 = default_b0(g.n, prec);
+        const int b0 = pick_b0(h, g.n, prec);
         const size_t w = prec == SEV_FP64 ? eig_workspace<double>(h, g.n, b0 > g.n - 1 ? g.n - 1 : b0)
                                           : eig_workspace<float>(h, g.n, b0 > g.n - 1 ? g.n - 1 : b0);
         if (w > need) need = w;
@@ -686,6 +704,22 @@ int sev_band_schedule(int n, int b0, int prec, int *bands, int max_bands) {
     int sched[40];
     const int ns = schedule(b0, prec == SEV_FP64 ? 8 : 4, sched);
     if (ns > max_bands) return -5;
+    for (int k = 0; k < ns; ++k) bands[k] = sched[k];
+    return ns;
+}
+
+int sev_eigvalsh_bands(sev_handle h, int n, int b0, int prec, int *bands, int max_bands) {
+    if (!h) return -1;
+    if (n < 0) return -2;
+    if (b0 < 0) return -3;
+    if (prec != SEV_FP64 && prec != SEV_MIXED) return -4;
+    if (!bands) return -5;
+    if (n <= 1) return 0;
+    if (b0 == 0) b0 = pick_b0(h, n, prec);
+    if (b0 > n - 1) b0 = n - 1 > 1 ? n - 1 : 1;
+    int sched[40];
+    const int ns = stages_for(h, n, b0, prec, sched);
+    if (ns > max_bands) return -6;
     for (int k = 0; k < ns; ++k) bands[k] = sched[k];
     return ns;
 }

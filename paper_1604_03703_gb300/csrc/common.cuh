@@ -50,6 +50,14 @@ struct TimedLaunch {
     cudaEvent_t e0, e1;
 };
 
+// Autotuned band schedule for one bucket of orders and precision: next[k]
+// is the width after 2^k (0: none), b0 the chosen first width (0: none).
+constexpr int kTuneWidths = 8;  // widths 1, 2, 4, ..., 128
+struct TunedBands {
+    int bucket = 0, prec = 0, b0 = 0;
+    int next[kTuneWidths] = {};
+};
+
 }  // namespace sev
 
 struct sev_ctx {
@@ -68,6 +76,7 @@ struct sev_ctx {
     int leaf_rows_override = 0;  // SEV_LEAF_ROWS: rows per tree-QR leaf (tests)
     int batch_b_fp64 = 0;        // band width chosen by sev_batch_autotune (0: default)
     int batch_b_mixed = 0;
+    std::vector<sev::TunedBands> tuned;  // sev_autotune results
     std::vector<sev::TimedLaunch> pending;
     std::vector<cudaEvent_t> event_pool;
     double tot_ms[sev::K_COUNT] = {};
@@ -808,6 +817,12 @@ size_t batch_mat_bytes();
 void batch_pack_mat(void *dst, void *A, double *eigs, int n, int lda);
 template <typename T>
 int launch_batch_fill(sev_ctx *h, int count, const void *mats, unsigned long long seed);
+
+// autotune.cu
+int tune_bucket(int n);
+const TunedBands *tuned_for(const sev_ctx *h, int n, int prec);
+int tuned_schedule(const TunedBands &t, int b0, int *out, int max_out);
+void tune_cache_load(sev_ctx *h);
 
 // update.cu: Y = sum of the K-split partial products (N x b each, split order)
 int launch_symm_reduce(sev_ctx *h, int N, int b, int splits, const float *part, float *Y);

@@ -16,7 +16,7 @@ static __device__ long long *sev_rtrace = nullptr;
 #define RTRACE(k, slot)                                                                       \
     do {                                                                                      \
         if (sev_rtrace && blockIdx.x == 0 && blockIdx.y == 0 && (threadIdx.x & 31) == 0 && (k) < 256) \
-            sev_rtrace[(k) * 4 + (slot)] = clock64();                                         \
+            sev_rtrace[(k) * 8 + (slot)] = clock64();                                         \
     } while (0)
 #else
 #define RTRACE(k, slot) \
@@ -143,9 +143,12 @@ __device__ __forceinline__ T reg_house(T (&x)[R], int k, T *vout) {
                     f2_add_sq(a0, (float)x[t]);
             }
         }
+        RTRACE(k, 4);
         const F2 acc = warp_sum_f2(f2_add(a0, a1));
+        RTRACE(k, 5);
         float tf, bf, iv;
         house_scalars_f2((float)alpha, acc, &tf, &bf, &iv);
+        RTRACE(k, 6);
         tau = (T)tf;
         beta = (T)bf;
         inv = (T)iv;

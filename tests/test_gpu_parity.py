@@ -454,3 +454,38 @@ def test_wait_limit_runs_out_then_handle_still_solves(torch_cuda, orc):
     ref = orc.eigvalsh(M, 1e-14)
     assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
     h.close()
+
+
+# ------------------------------------------------------------- autotuner
+def test_autotune_choice_is_the_schedule_run(torch_cuda, orc, tmp_path, monkeypatch):
+    """sev_autotune measures every candidate b0 and band stage at the order
+    and keeps the cheapest path; sev_eigvalsh with b0 = 0 then runs exactly
+    that path (reported by sev_eigvalsh_bands) and stays correct; the cache
+    file brings the same choice to a new handle."""
+    torch = torch_cuda
+    from paper_1604_03703_gb300 import _lib, api
+    from paper_1604_03703_gb300 import build as B
+
+    B.build()
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("SEV_TUNE_CACHE", str(cache))
+    h = api.Handle(0)
+    n = 1500
+    bands, ms = h.autotune(n, _lib.SEV_MIXED, 0)
+    h.raise_device_error("autotune")
+    assert bands[0] in (32, 64, 128) and bands[-1] == 1 and ms > 0
+    assert all(b % c == 0 for b, c in zip(bands[:-1], bands[1:]) if c > 1)
+    assert h.eigvalsh_bands(n, 0, _lib.SEV_MIXED) == bands
+    # a fixed b0 keeps its own tuned stage path from that width
+    b128, _ = h.autotune(n, _lib.SEV_MIXED, 128)
+    assert b128[0] == 128 and h.eigvalsh_bands(n, 128, _lib.SEV_MIXED) == b128
+    assert h.eigvalsh_bands(n, 0, _lib.SEV_MIXED)[0] == bands[0]  # the tuned b0 is kept
+    A = I.semicircle(n, 9500)
+    got = h.eigvalsh(dev(torch, A, torch.float32), 0).cpu().numpy()
+    h.raise_device_error()
+    lam = np.linalg.eigvalsh(A)
+    assert np.abs(got - lam).max() <= 1e-4 * np.abs(lam).max()
+    h.close()
+    h2 = api.Handle(0)
+    assert h2.eigvalsh_bands(n, 128, _lib.SEV_MIXED) == b128
+    h2.close()
