@@ -254,13 +254,15 @@ int sev_band_schedule(int n, int b0, int prec, int *bands, int max_bands);
  * appended there, keyed by the GPU's name, and read back by sev_create.
  *   bands      host, receives the widths from b0 (b0 as given, or the tuned
  *              one) down to 1; max_bands entries available
+ *   nbands     host, receives the number of widths written (0 for n < 4)
  *   best_ms    host, may be NULL: the predicted milliseconds of the
  *              reductions (full-to-band plus band stages) along that path
- * Returns the number of widths written (0 for n < 4), -i for invalid
- * argument i, or an SEV_ERR_* code.  Allocates an n x n test matrix and
- * the workspace, and synchronises the handle's stream.
+ * Returns SEV_OK, -i for invalid argument i (-6: max_bands too small for
+ * the path), or an SEV_ERR_* code.  Allocates an n x n test matrix and the
+ * workspace, and synchronises the handle's stream.
  */
-int sev_autotune(sev_handle handle, int n, int prec, int b0, int *bands, int max_bands, double *best_ms);
+int sev_autotune(sev_handle handle, int n, int prec, int b0, int *bands, int max_bands, int *nbands,
+                 double *best_ms);
 
 /* The band widths sev_eigvalsh(handle, n, ., ., b0, prec, .) runs (host
  * only, no device work): as sev_band_schedule, but with this handle's

@@ -58,7 +58,7 @@ SIGNATURES = {
     "sev_batch_autotune": (_i, [_vp, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i)]),
     "sev_diag_house_scalars": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _vp]),
     "sev_band_schedule": (_i, [_i, _i, _i, ctypes.POINTER(_i), _i]),
-    "sev_autotune": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_d)]),
+    "sev_autotune": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_i), _i, ctypes.POINTER(_i), ctypes.POINTER(_d)]),
     "sev_eigvalsh_bands": (_i, [_vp, _i, _i, _i, ctypes.POINTER(_i), _i]),
 }
 

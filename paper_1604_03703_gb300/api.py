@@ -178,11 +178,11 @@ class Handle:
         (widths from b0 down to 1, predicted reduction milliseconds)."""
         self._sync_stream()
         bands = (ctypes.c_int * 16)()
+        nb = ctypes.c_int()
         ms = ctypes.c_double()
-        k = self._lib.sev_autotune(self._h, int(n), int(prec), int(b0), bands, 16, ctypes.byref(ms))
-        if k < 0 or k > 16:
-            check(k if k < 0 else -6, "sev_autotune")
-        return list(bands[:k]), ms.value
+        check(self._lib.sev_autotune(self._h, int(n), int(prec), int(b0), bands, 16, ctypes.byref(nb), ctypes.byref(ms)),
+              "sev_autotune")
+        return list(bands[:nb.value]), ms.value
 
     def eigvalsh_bands(self, n: int, b0: int, prec: int):
         """The band widths eigvalsh(n, b0, prec) runs on this handle."""

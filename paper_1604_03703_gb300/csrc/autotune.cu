@@ -262,7 +262,8 @@ static int autotune_t(sev_ctx *h, int n, int prec, int b0_req, TunedBands *out, 
 
 }  // namespace sev
 
-extern "C" int sev_autotune(sev_handle h, int n, int prec, int b0, int *bands, int max_bands, double *best_ms) {
+extern "C" int sev_autotune(sev_handle h, int n, int prec, int b0, int *bands, int max_bands, int *nbands,
+                            double *best_ms) {
     using namespace sev;
     if (!h) return -1;
     if (n < 0) return -2;
@@ -270,7 +271,9 @@ extern "C" int sev_autotune(sev_handle h, int n, int prec, int b0, int *bands, i
     if (b0 < 0) return -4;
     if (!bands) return -5;
     if (max_bands < 1) return -6;
-    if (n < 4) return 0;  // nothing to reduce
+    if (!nbands) return -7;
+    *nbands = 0;
+    if (n < 4) return SEV_OK;  // nothing to reduce
     if (cudaSetDevice(h->device) != cudaSuccess) return SEV_ERR_CUDA;
     TunedBands t;
     const int rc = prec == SEV_FP64 ? autotune_t<double>(h, n, prec, b0, &t, best_ms)
@@ -287,5 +290,6 @@ extern "C" int sev_autotune(sev_handle h, int n, int prec, int b0, int *bands, i
     if (ns == 0) return SEV_ERR_UNSUPPORTED;
     if (ns > max_bands) return -6;
     for (int k = 0; k < ns; ++k) bands[k] = sched[k];
-    return ns;
+    *nbands = ns;
+    return SEV_OK;
 }
