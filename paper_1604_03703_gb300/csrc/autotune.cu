@@ -198,9 +198,10 @@ static int autotune_t(sev_ctx *h, int n, int prec, int b0_req, TunedBands *out, 
     for (auto &r : cost)
         for (double &x : r) x = -1.0;
     const int nwarm = n < 1024 ? n : 1024;
+    const int targets[] = {64, 32, 16, 8, 4, 2, 1};
     for (int b : widths) {
         if (rc || b > bmax || b >= n - 1) continue;
-        for (int w : widths) {
+        for (int w : targets) {
             if (rc) break;
             if (w >= b || !stage_ok<T>(h, b, w)) continue;
             tune_fill_band_kernel<T><<<grid, 256, 0, h->stream>>>(nwarm, b, AB, ldab, 0x7A11ull);

@@ -77,8 +77,7 @@ struct RowBlocks {
 // reduced together so their shuffle chains overlap.
 template <typename T, int R, int Q>
 __device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const bool (&act)[R], T tau,
-                                          const T (&cm)[Q], int q0 = 0) {
-    // columns q < q0 (warp-uniform) are finished: skipped outright
+                                          const T (&cm)[Q]) {
     T d[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) d[q] = T(0);
@@ -86,15 +85,12 @@ __device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const 
     for (int t = 0; t < R; ++t)
         if (act[t]) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q >= q0) d[q] = fmat(vr[t], a[q][t], d[q]);
+            for (int q = 0; q < Q; ++q) d[q] = fmat(vr[t], a[q][t], d[q]);
         }
 #pragma unroll
-    for (int q = 0; q < Q; ++q)
-        if (q >= q0) {
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
-        }
+        for (int q = 0; q < Q; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
     T sc[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) sc[q] = tau * d[q] * cm[q];
@@ -102,8 +98,7 @@ __device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const 
     for (int t = 0; t < R; ++t)
         if (act[t]) {
 #pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q >= q0) a[q][t] = fmat(-sc[q], vr[t], a[q][t]);
+            for (int q = 0; q < Q; ++q) a[q][t] = fmat(-sc[q], vr[t], a[q][t]);
         }
 }
 
@@ -274,9 +269,7 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
             for (int q = 0; q < Q; ++q)
                 if (q == q1) cm[q] = T(0);
         }
-        // this warp's columns c = warp + NW q are finished for q < q0
-        const int q0 = k < warp ? 0 : (k - warp) / NW + 1;
-        if (tk != T(0) && q0 < Q) reg_apply<T, R, Q>(a, vr, act, tk, cm, q0);
+        if (tk != T(0)) reg_apply<T, R, Q>(a, vr, act, tk, cm);
         if (k1 < nc && (k1 % NW) == warp) RTRACE(k, 3);
         __syncthreads();
     }
