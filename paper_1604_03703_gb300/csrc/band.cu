@@ -81,9 +81,13 @@ __device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, i
 // Shared memory of one chase: U, U T, the block X being updated, W, T, a
 // small product Z, tau, the double-buffered reflector of the register QR and
 // a reduction scratch.
+// Shared memory of one chase: U, U T, the block X being updated, W, T, a
+// small product Z, tau, the double-buffered reflector of the register QR, a
+// reduction scratch and (register path) a second block buffer Xb for the
+// rows above the qr rows, loaded while the QR runs.
 template <typename T>
 struct ChaseSmem {
-    T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau, *vs;
+    T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau, *vs, *Xb;
     double *red;
     int ldb1, ldh1;
     __device__ ChaseSmem(unsigned char *base, int b, int h) {
@@ -100,22 +104,35 @@ struct ChaseSmem {
         size_t off = (size_t)((unsigned char *)(vs + 2 * 128) - base);
         off = (off + 15) & ~(size_t)15;
         red = (double *)(base + off);
+        Xb = (T *)(base + off + 32 * sizeof(double));
     }
 };
 
+// Register tile of the chase QR, run by warps 0-3: rows up to 32 R (R = 0:
+// the shared-memory cta_qr by the whole CTA), columns up to 4 Q.
+__host__ __device__ constexpr int chase_tile_r(int b) { return b <= 32 ? 1 : (b <= 64 ? 2 : (b <= 128 ? 4 : 0)); }
+__host__ __device__ constexpr int chase_tile_q(int h) {
+    return h <= 4 ? 1 : (h <= 8 ? 2 : (h <= 16 ? 4 : (h <= 32 ? 8 : (h <= 64 ? 16 : 0))));
+}
+
 template <typename T>
-size_t band_smem_bytes(int b, int h) {
+static size_t band_smem_base(int b, int h) {
     const size_t ldb1 = b + 1, ldh1 = h + 1;
     size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h + 2 * 128;
     size_t bytes = e * sizeof(T);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + 32 * sizeof(double);
 }
+// The register path needs the Xb buffer as well.
+template <typename T>
+static size_t band_smem_reg(int b, int h) {
+    return band_smem_base<T>(b, h) + sizeof(T) * (size_t)(b + 1) * b;
+}
 
-// Register tile of the chase QR (8 warps): rows up to 32 R (R = 0: the
-// shared-memory cta_qr), columns up to 8 Q.
-__host__ __device__ constexpr int chase_tile_r(int b) { return b <= 32 ? 1 : (b <= 64 ? 2 : (b <= 128 ? 4 : 0)); }
-__host__ __device__ constexpr int chase_tile_q(int h) { return h <= 8 ? 1 : (h <= 16 ? 2 : (h <= 32 ? 4 : (h <= 64 ? 8 : 0))); }
+template <typename T>
+size_t band_smem_bytes(int b, int h) {
+    return band_smem_base<T>(b, h);
+}
 
 // One chase (i, j) performed by the whole CTA.  RQ, QQ > 0: the n_r x h QR
 // runs on a register tile of 32 RQ x 8 QQ (reg_qr); 0: on shared memory.
@@ -142,34 +159,60 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     BTRACE(0);
     int nr;
     if constexpr (RQ > 0) {
-        // 1. QR of the n_r x h block in registers (lane rows, warp-cyclic columns)
         const int warp = tid >> 5, lane = tid & 31;
-        T a[QQ][RQ];
+        nr = n_r - 1 < h ? n_r - 1 : h;
+        if (nr < 0) nr = 0;
+        if (warp < 4) {
+            // 1. warps 0-3: QR of the n_r x h block in registers (lane rows,
+            //    warp-cyclic columns), one warp per scheduler
+            T a[QQ][RQ];
 #pragma unroll
-        for (int q = 0; q < QQ; ++q)
+            for (int q = 0; q < QQ; ++q)
 #pragma unroll
-            for (int t = 0; t < RQ; ++t) {
-                const int r = lane + 32 * t, c = warp + 8 * q;
-                a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
-            }
-        BTRACE(1);
-        nr = reg_qr<T, RQ, QQ, 8>(a, n_r, h, 0, S.vs, S.tau);
-        BTRACE(2);
-        // 2. B[qr rows, qr cols] = [R; 0]; U explicit into shared memory
-#pragma unroll
-        for (int q = 0; q < QQ; ++q)
-#pragma unroll
-            for (int t = 0; t < RQ; ++t) {
-                const int r = lane + 32 * t, c = warp + 8 * q;
-                if (r < n_r && c < h) {
-                    bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, r <= c ? a[q][t] : T(0), bad);
-                    if (c < nr) S.Us[r + (size_t)c * ldb1] = r < c ? T(0) : (r == c ? T(1) : a[q][t]);
+                for (int t = 0; t < RQ; ++t) {
+                    const int r = lane + 32 * t, c = warp + 4 * q;
+                    a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
                 }
+            BTRACE(1);
+            reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau);
+            BTRACE(2);
+            // 2. B[qr rows, qr cols] = [R; 0]; U explicit into shared memory
+#pragma unroll
+            for (int q = 0; q < QQ; ++q)
+#pragma unroll
+                for (int t = 0; t < RQ; ++t) {
+                    const int r = lane + 32 * t, c = warp + 4 * q;
+                    if (r < n_r && c < h) {
+                        bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, r <= c ? a[q][t] : T(0), bad);
+                        if (c < nr) S.Us[r + (size_t)c * ldb1] = r < c ? T(0) : (r == c ? T(1) : a[q][t]);
+                    }
+                }
+        } else if (nr > 0) {
+            // warps 4-7 meanwhile: the diagonal block (stored lower triangle,
+            // read down its columns, then mirrored) and the rows above the qr
+            // rows (element (row, col) stored as (col, row): read along col)
+            const int t4 = tid - 128;
+            batched_copy<T>(
+                n_r * n_r, t4, 128,
+                [&](int k) {
+                    const int r = k % n_r, c = k / n_r;
+                    return r >= c ? bld(AB, ldab, n, o_qr_r + r, o_qr_r + c, bad) : T(0);
+                },
+                [&](int k, T v) {
+                    const int r = k % n_r, c = k / n_r;
+                    if (r >= c) S.Xs[r + (size_t)c * ldb1] = v;
+                });
+            batched_copy<T>(
+                o_v * n_r, t4, 128, [&](int k) { return bld(AB, ldab, n, o_qr_r + k % n_r, o_up_c + k / n_r, bad); },
+                [&](int k, T v) { S.Xb[k / n_r + (size_t)(k % n_r) * ldb1] = v; });
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+            for (int idx = t4; idx < n_r * n_r; idx += 128) {
+                const int r = idx % n_r, c = idx / n_r;
+                if (r < c) S.Xs[r + (size_t)c * ldb1] = S.Xs[c + (size_t)r * ldb1];
             }
-        if (nr == 0) {
-            __syncthreads();
-            return;
         }
+        __syncthreads();
+        if (nr == 0) return;
     } else {
         // 1. QR of the n_r x h block
         batched_copy<T>(
@@ -205,23 +248,26 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     __syncthreads();
     BTRACE(3);
     // 4. the qr-row diagonal block X_d (n_r x n_r): two-sided update
-    // (the stored lower triangle, read down its columns, then mirrored in shared memory)
-    batched_copy<T>(
-        n_r * n_r, tid, nt,
-        [&](int k) {
-            const int r = k % n_r, c = k / n_r;
-            return r >= c ? bld(AB, ldab, n, o_qr_r + r, o_qr_r + c, bad) : T(0);
-        },
-        [&](int k, T v) {
-            const int r = k % n_r, c = k / n_r;
-            if (r >= c) S.Xs[r + (size_t)c * ldb1] = v;
-        });
-    __syncthreads();
-    for (int idx = tid; idx < n_r * n_r; idx += nt) {
-        const int r = idx % n_r, c = idx / n_r;
-        if (r < c) S.Xs[r + (size_t)c * ldb1] = S.Xs[c + (size_t)r * ldb1];
+    // (the stored lower triangle, read down its columns, then mirrored in
+    // shared memory; on the register path it is already there)
+    if constexpr (RQ == 0) {
+        batched_copy<T>(
+            n_r * n_r, tid, nt,
+            [&](int k) {
+                const int r = k % n_r, c = k / n_r;
+                return r >= c ? bld(AB, ldab, n, o_qr_r + r, o_qr_r + c, bad) : T(0);
+            },
+            [&](int k, T v) {
+                const int r = k % n_r, c = k / n_r;
+                if (r >= c) S.Xs[r + (size_t)c * ldb1] = v;
+            });
+        __syncthreads();
+        for (int idx = tid; idx < n_r * n_r; idx += nt) {
+            const int r = idx % n_r, c = idx / n_r;
+            if (r < c) S.Xs[r + (size_t)c * ldb1] = S.Xs[c + (size_t)r * ldb1];
+        }
+        __syncthreads();
     }
-    __syncthreads();
     BTRACE(6);
     // W_d = X_d (U T)
     cta_gemm<T, false, false>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
@@ -277,7 +323,11 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         const int a_end = part == 0 ? o_v : n_c;
         for (int a0 = a_begin; a0 < a_end; a0 += b) {
             const int rows = min(b, a_end - a0);
-            if (part == 0) {
+            // the block of this chunk: Xb for the rows above on the register
+            // path (loaded during the QR; there is one chunk of o_v < b rows)
+            T *X = (RQ > 0 && part == 0) ? S.Xb : S.Xs;
+            if (part == 0 && RQ > 0) {
+            } else if (part == 0) {
                 // rows above the qr rows: element (row, col) is stored as (col, row), contiguous
                 // along col -- consecutive threads take consecutive columns
                 batched_copy<T>(
@@ -292,18 +342,18 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
             }
             __syncthreads();
             if (part == 1 && a0 == a_begin) BTRACE(11);
-            cta_gemm<T, false, false>(rows, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
+            cta_gemm<T, false, false>(rows, nr, n_r, T(1), X, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
             __syncthreads();
             if (part == 1 && a0 == a_begin) BTRACE(12);
             // X <- X - W U^T: register-tiled for wide blocks, else folded into the stores
             const bool tiled = n_r >= 64;
             if (tiled) {
-                cta_gemm<T, false, true>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
+                cta_gemm<T, false, true>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, T(1), X, ldb1);
                 __syncthreads();
             }
             if (part == 1 && a0 == a_begin) BTRACE(13);
             auto updated = [&](int r, int c) {
-                T v = S.Xs[r + (size_t)c * ldb1];
+                T v = X[r + (size_t)c * ldb1];
                 if (!tiled)
                     for (int m = 0; m < nr; ++m) v -= S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
                 return v;
@@ -387,24 +437,32 @@ int launch_band_to_band(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, void 
     const int nsweeps = band_num_sweeps(n, h);
     if (nsweeps <= 0) return SEV_OK;
     if (ws_bytes < band_workspace(n, b, h)) return SEV_ERR_WORKSPACE;
-    const size_t smem = band_smem_bytes<T>(b, h);
+    size_t smem = band_smem_bytes<T>(b, h);
     if (smem > hd->smem_optin) return SEV_ERR_UNSUPPORTED;
     Carver c(ws);
     int *progress = c.take<int>((size_t)nsweeps + 1);
     int *ctr = c.take<int>(1);
     SEV_CUDA(cudaMemsetAsync(progress, 0, sizeof(int) * ((size_t)nsweeps + 1), hd->stream));
     SEV_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), hd->stream));
+    // register path when its tile and its second block buffer fit
     const int RQ = chase_tile_r(b), QQ = chase_tile_q(h);
     auto kern = band_chase_kernel<T, 0, 0>;
-    if (RQ == 1 && QQ == 1) kern = band_chase_kernel<T, 1, 1>;
-    if (RQ == 1 && QQ == 2) kern = band_chase_kernel<T, 1, 2>;
-    if (RQ == 2 && QQ == 1) kern = band_chase_kernel<T, 2, 1>;
-    if (RQ == 2 && QQ == 2) kern = band_chase_kernel<T, 2, 2>;
-    if (RQ == 2 && QQ == 4) kern = band_chase_kernel<T, 2, 4>;
-    if (RQ == 4 && QQ == 1) kern = band_chase_kernel<T, 4, 1>;
-    if (RQ == 4 && QQ == 2) kern = band_chase_kernel<T, 4, 2>;
-    if (RQ == 4 && QQ == 4) kern = band_chase_kernel<T, 4, 4>;
-    if (RQ == 4 && QQ == 8) kern = band_chase_kernel<T, 4, 8>;
+    if (RQ > 0 && QQ > 0 && band_smem_reg<T>(b, h) <= hd->smem_optin) {
+        smem = band_smem_reg<T>(b, h);
+        if (RQ == 1 && QQ == 1) kern = band_chase_kernel<T, 1, 1>;
+        if (RQ == 1 && QQ == 2) kern = band_chase_kernel<T, 1, 2>;
+        if (RQ == 1 && QQ == 4) kern = band_chase_kernel<T, 1, 4>;
+        if (RQ == 2 && QQ == 1) kern = band_chase_kernel<T, 2, 1>;
+        if (RQ == 2 && QQ == 2) kern = band_chase_kernel<T, 2, 2>;
+        if (RQ == 2 && QQ == 4) kern = band_chase_kernel<T, 2, 4>;
+        if (RQ == 2 && QQ == 8) kern = band_chase_kernel<T, 2, 8>;
+        if (RQ == 4 && QQ == 1) kern = band_chase_kernel<T, 4, 1>;
+        if (RQ == 4 && QQ == 2) kern = band_chase_kernel<T, 4, 2>;
+        if (RQ == 4 && QQ == 4) kern = band_chase_kernel<T, 4, 4>;
+        if (RQ == 4 && QQ == 8) kern = band_chase_kernel<T, 4, 8>;
+        if (RQ == 4 && QQ == 16) kern = band_chase_kernel<T, 4, 16>;
+        if (kern == band_chase_kernel<T, 0, 0>) smem = band_smem_bytes<T>(b, h);
+    }
     SEV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));

@@ -216,12 +216,22 @@ __device__ __forceinline__ T reg_house(T (&x)[R], int k, T *vout) {
 // >= m and columns >= nc zero), r = min(nc, m - 1) reflectors.  On return
 // column c holds R above and on the diagonal and v_c below it (unit
 // diagonal implicit); taus[c] = tau_c.  vs: 2 x 32R shared scratch.
-template <typename T, int R, int Q, int NW>
+// Barrier of the warps running reg_qr: the whole CTA (BAR = 0) or named
+// barrier BAR over warps 0 .. NW-1 (the rest of the CTA does other work).
+template <int NW, int BAR>
+__device__ __forceinline__ void reg_sync() {
+    if constexpr (BAR == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NW * 32) : "memory");
+}
+
+template <typename T, int R, int Q, int NW, int BAR = 0>
 __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = nc < m - 1 ? nc : m - 1;
     if (r <= 0) {
-        __syncthreads();
+        reg_sync<NW, BAR>();
         return 0;
     }
     const RowBlocks<R> blk(bstack);
@@ -229,7 +239,7 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
         const T t0 = reg_house<T, R>(a[0], 0, vs);
         if (lane == 0) taus[0] = t0;
     }
-    __syncthreads();
+    reg_sync<NW, BAR>();
     for (int k = 0; k < r; ++k) {
         const T *v = vs + (k & 1) * (32 * R);
         const T tk = taus[k];
@@ -271,7 +281,7 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
         }
         if (tk != T(0)) reg_apply<T, R, Q>(a, vr, act, tk, cm);
         if (k1 < nc && (k1 % NW) == warp) RTRACE(k, 3);
-        __syncthreads();
+        reg_sync<NW, BAR>();
     }
     return r;
 }
