@@ -59,21 +59,24 @@ __host__ __device__ __forceinline__ int band_num_chases(int n, int b, int h, int
 __host__ __device__ __forceinline__ int band_num_sweeps(int n, int h) { return n >= 2 ? (n - 2) / h : 0; }
 
 // Band element (r, c) with r >= c; out-of-range indices are a bug: they are
-// not dereferenced, the CTA's flag is set and 0 is returned.
+// not dereferenced, the thread's flag `bad` is set and 0 is returned.  The
+// flag is a register (OR-ed over the CTA at the end of the kernel): a flag
+// in memory would be a store between consecutive loads and keep them from
+// being in flight together.
 template <typename T>
-__device__ __forceinline__ T bld(const T *AB, int ldab, int n, int r, int c, int *bad) {
+__device__ __forceinline__ T bld(const T *AB, int ldab, int n, int r, int c, int &bad) {
     const int d = r - c;
     if (d < 0 || d >= ldab || r >= n || c < 0) {
-        *bad = 1;
+        bad = 1;
         return T(0);
     }
     return __ldcg(AB + d + (size_t)c * ldab);
 }
 template <typename T>
-__device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, int *bad) {
+__device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, int &bad) {
     const int d = r - c;
     if (d < 0 || d >= ldab || r >= n || c < 0) {
-        *bad = 1;
+        bad = 1;
         return;
     }
     AB[d + (size_t)c * ldab] = v;
@@ -91,7 +94,7 @@ struct ChaseSmem {
     double *red;
     int ldb1, ldh1;
     __device__ ChaseSmem(unsigned char *base, int b, int h) {
-        ldb1 = b + 1;
+        ldb1 = b + 4;  // a multiple of 4: 16-byte aligned columns for vector loads
         ldh1 = h + 1;
         Us = (T *)base;
         UTs = Us + (size_t)ldb1 * h;
@@ -117,7 +120,7 @@ __host__ __device__ constexpr int chase_tile_q(int h) {
 
 template <typename T>
 static size_t band_smem_base(int b, int h) {
-    const size_t ldb1 = b + 1, ldh1 = h + 1;
+    const size_t ldb1 = b + 4, ldh1 = h + 1;
     size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h + 2 * 128;
     size_t bytes = e * sizeof(T);
     bytes = (bytes + 15) & ~(size_t)15;
@@ -126,7 +129,7 @@ static size_t band_smem_base(int b, int h) {
 // The register path needs the Xb buffer as well.
 template <typename T>
 static size_t band_smem_reg(int b, int h) {
-    return band_smem_base<T>(b, h) + sizeof(T) * (size_t)(b + 1) * b;
+    return band_smem_base<T>(b, h) + sizeof(T) * (size_t)(b + 4) * b;
 }
 
 template <typename T>
@@ -137,7 +140,7 @@ size_t band_smem_bytes(int b, int h) {
 // One chase (i, j) performed by the whole CTA.  RQ, QQ > 0: the n_r x h QR
 // runs on a register tile of 32 RQ x 8 QQ (reg_qr); 0: on shared memory.
 template <typename T, int RQ, int QQ>
-__device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, ChaseSmem<T> &S, int *bad) {
+__device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, ChaseSmem<T> &S, int &bad) {
     const int o_qr_r = (i - 1) * h + (j - 1) * b + h;
     int o_qr_c, o_v, o_up_c, lim;
     if (j == 1) {
@@ -244,7 +247,9 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         __syncthreads();
         cta_form_t(n_r, nr, S.Us, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
     }
-    cta_gemm<T, false, false>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, T(0), S.UTs, ldb1);
+    constexpr bool kVec = sizeof(T) == 4;
+    cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, 0, nullptr, 0, nullptr, 0, T(0), S.UTs,
+                                 ldb1);
     __syncthreads();
     BTRACE(3);
     // 4. the qr-row diagonal block X_d (n_r x n_r): two-sided update
@@ -270,7 +275,8 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     }
     BTRACE(6);
     // W_d = X_d (U T)
-    cta_gemm<T, false, false>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
+    cta_mm<T, 4, 4, false, kVec>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, 0, nullptr, 0, nullptr, 0, T(0), S.Ws,
+                                 ldb1);
     __syncthreads();
     BTRACE(7);
     // S = U^T W_d
@@ -287,15 +293,16 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     }
     __syncthreads();
     // V_d = -W_d + 1/2 U Z  (into Ws)
-    cta_gemm<T, false, false>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, T(-1), S.Ws, ldb1);
+    cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, 0, nullptr, 0, nullptr, 0, T(-1), S.Ws,
+                                 ldb1);
     __syncthreads();
     BTRACE(9);
     // X_d += U V_d^T + V_d U^T, lower half stored: register-tiled products for
     // wide blocks, one element per thread for narrow ones (more threads busy)
     if (n_r >= 64) {
-        cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, T(1), S.Xs, ldb1);
-        __syncthreads();
-        cta_gemm<T, false, true>(n_r, n_r, nr, T(1), S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs, ldb1);
+        // one pass over the block: X_d += [U V_d] [V_d U]^T
+        cta_mm<T, 8, 8, true, kVec>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, nr, S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs,
+                                    ldb1);
         __syncthreads();
         BTRACE(10);
         for (int idx = tid; idx < n_r * n_r; idx += nt) {
@@ -342,13 +349,15 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
             }
             __syncthreads();
             if (part == 1 && a0 == a_begin) BTRACE(11);
-            cta_gemm<T, false, false>(rows, nr, n_r, T(1), X, ldb1, S.UTs, ldb1, T(0), S.Ws, ldb1);
+            cta_mm<T, 4, 4, false, kVec>(rows, nr, n_r, T(1), X, ldb1, S.UTs, ldb1, 0, nullptr, 0, nullptr, 0, T(0),
+                                         S.Ws, ldb1);
             __syncthreads();
             if (part == 1 && a0 == a_begin) BTRACE(12);
             // X <- X - W U^T: register-tiled for wide blocks, else folded into the stores
             const bool tiled = n_r >= 64;
             if (tiled) {
-                cta_gemm<T, false, true>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, T(1), X, ldb1);
+                cta_mm<T, 8, 8, true, kVec>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, 0, nullptr, 0, nullptr, 0,
+                                            T(1), X, ldb1);
                 __syncthreads();
             }
             if (part == 1 && a0 == a_begin) BTRACE(13);
@@ -380,8 +389,8 @@ __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int 
                                                                int *progress, int *sweep_ctr, int *err) {
     extern __shared__ __align__(16) unsigned char smem[];
     ChaseSmem<T> S(smem, b, h);
-    __shared__ int s_sweep, s_abort, s_bad;
-    if (threadIdx.x == 0) s_bad = 0;
+    __shared__ int s_sweep, s_abort;
+    int bad = 0;  // this thread met an index outside the band
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -414,15 +423,14 @@ __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int 
                 __syncthreads();
                 if (s_abort) return;
             }
-            band_chase<T, RQ, QQ>(AB, ldab, n, b, h, i, j, S, &s_bad);
+            band_chase<T, RQ, QQ>(AB, ldab, n, b, h, i, j, S, bad);
             __syncthreads();
             // the release store orders the CTA's writes (made visible to
             // thread 0 by the barrier above) before the progress flag
             if (threadIdx.x == 0) st_release(&progress[s], j);
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0 && s_bad) latch_error(err, SEV_ERR_INTERNAL);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) latch_error(err, SEV_ERR_INTERNAL);
 }
 
 size_t band_workspace(int n, int b, int h) {

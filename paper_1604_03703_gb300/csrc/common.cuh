@@ -625,6 +625,97 @@ __device__ void cta_gemm(int M, int N, int K, T alpha, const T *A, int lda, cons
     }
 }
 
+// C = alpha * (A1 B1 + A2 B2) + beta * C on shared-memory operands with
+// register tiles: every thread computes TM x TN outputs, rows m0 .. m0+TM-1
+// (consecutive: threads with consecutive blocks read consecutive addresses)
+// and columns n0 .. n0+TN-1 (threads of a warp mostly share them: broadcast
+// reads).  A_p(m, k) = A_p[m + k lda] (m contiguous); B_p(k, n) =
+// B_p[n + k ldb] when BT (n contiguous) else B_p[k + n ldb].  The second
+// pair is skipped when K2 = 0.  VEC (T = float only): lda, ldb, ldc are
+// multiples of 4 and the bases 16-byte aligned, so full tiles use float4
+// loads; ragged tiles fall back to clamped scalar reads (never outside the
+// M x K / K x N operands).  Each output sums its k terms in order (A1 B1
+// first); no barrier inside.
+template <typename T, int TM, int TN, bool BT, bool VEC>
+__device__ void cta_mm(int M, int N, int K1, T alpha, const T *A1, int lda1, const T *B1, int ldb1, int K2,
+                       const T *A2, int lda2, const T *B2, int ldb2, T beta, T *C, int ldc) {
+    static_assert(!VEC || (sizeof(T) == 4 && TM % 4 == 0 && (!BT || TN % 4 == 0)), "vector loads need float tiles");
+    const int Mb = (M + TM - 1) / TM, Nb = (N + TN - 1) / TN;
+    for (int blk = threadIdx.x; blk < Mb * Nb; blk += blockDim.x) {
+        const int m0 = (blk % Mb) * TM, n0 = (blk / Mb) * TN;
+        const bool full = m0 + TM <= M && n0 + TN <= N;
+        T acc[TM][TN];
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+        for (int p = 0; p < 2; ++p) {
+            const int K = p == 0 ? K1 : K2;
+            const T *A = p == 0 ? A1 : A2;
+            const T *B = p == 0 ? B1 : B2;
+            const int lda = p == 0 ? lda1 : lda2, ldb = p == 0 ? ldb1 : ldb2;
+            if (K <= 0) continue;
+            if (VEC && full) {
+#pragma unroll 2
+                for (int k = 0; k < K; ++k) {
+                    T a[TM], bb[TN];
+#pragma unroll
+                    for (int i = 0; i < TM; i += 4) {
+                        const float4 v = *reinterpret_cast<const float4 *>(A + m0 + i + (size_t)k * lda);
+                        a[i] = v.x;
+                        a[i + 1] = v.y;
+                        a[i + 2] = v.z;
+                        a[i + 3] = v.w;
+                    }
+                    if constexpr (BT) {
+#pragma unroll
+                        for (int j = 0; j < TN; j += 4) {
+                            const float4 v = *reinterpret_cast<const float4 *>(B + n0 + j + (size_t)k * ldb);
+                            bb[j] = v.x;
+                            bb[j + 1] = v.y;
+                            bb[j + 2] = v.z;
+                            bb[j + 3] = v.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) bb[j] = B[k + (size_t)(n0 + j) * ldb];
+                    }
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * bb[j];
+                }
+            } else {
+                int mi[TM], nj[TN];
+#pragma unroll
+                for (int i = 0; i < TM; ++i) mi[i] = m0 + i < M ? m0 + i : M - 1;
+#pragma unroll
+                for (int j = 0; j < TN; ++j) nj[j] = n0 + j < N ? n0 + j : N - 1;
+#pragma unroll 2
+                for (int k = 0; k < K; ++k) {
+                    T a[TM], bb[TN];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i) a[i] = A[mi[i] + (size_t)k * lda];
+#pragma unroll
+                    for (int j = 0; j < TN; ++j) bb[j] = BT ? B[nj[j] + (size_t)k * ldb] : B[k + (size_t)nj[j] * ldb];
+#pragma unroll
+                    for (int i = 0; i < TM; ++i)
+#pragma unroll
+                        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * bb[j];
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < TM; ++i)
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                if (m0 + i >= M || n0 + j >= N) continue;
+                T *c = &C[(m0 + i) + (size_t)(n0 + j) * ldc];
+                *c = (beta == T(0)) ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
+            }
+    }
+}
+
 // --------------------------------------------------- blocked (level-3) QR
 // Householder QR of the m x nc block P in panels of kQrNB columns: each
 // panel is factorised column by column (cta_qr, reflectors applied inside
