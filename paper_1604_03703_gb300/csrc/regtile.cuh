@@ -102,6 +102,104 @@ __device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const 
         }
 }
 
+// Two FP32 FMAs in one instruction (fma.rn.f32x2: each lane rounded once,
+// the same results as two fmaf).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n"
+        " .reg .b64 ra, rb, rc, rd;\n"
+        " mov.b64 ra, {%2, %3};\n"
+        " mov.b64 rb, {%4, %5};\n"
+        " mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n"
+        " mov.b64 {%0, %1}, rd;\n"
+        "}\n"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+
+// Warp sums of Q per-lane values (Q = 2, 4, 8) by a transposing butterfly:
+// at each of the first log2 Q levels a lane keeps half of its remaining
+// values and sends the other half to its partner, so the shuffles total
+// Q - 1 + (5 - log2 Q) + Q (the last Q broadcast the sums) instead of 5 Q.
+// On return d[q] holds the sum over the 32 lanes (every lane).
+template <int Q>
+__device__ __forceinline__ void warp_sums_x(float (&d)[Q]) {
+    const int lane = threadIdx.x & 31;
+    float c;
+    if constexpr (Q == 8) {
+        const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
+        float a4[4], b2[2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a4[j] = (u16 ? d[j + 4] : d[j]) + __shfl_xor_sync(0xffffffffu, u16 ? d[j] : d[j + 4], 16);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) b2[j] = (u8 ? a4[j + 2] : a4[j]) + __shfl_xor_sync(0xffffffffu, u8 ? a4[j] : a4[j + 2], 8);
+        c = (u4 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, u4 ? b2[0] : b2[1], 4);
+        c += __shfl_xor_sync(0xffffffffu, c, 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) d[q] = __shfl_sync(0xffffffffu, c, ((q >> 2) & 1) * 16 + ((q >> 1) & 1) * 8 + (q & 1) * 4);
+    } else if constexpr (Q == 4) {
+        const bool u16 = lane & 16, u8 = lane & 8;
+        float b2[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) b2[j] = (u16 ? d[j + 2] : d[j]) + __shfl_xor_sync(0xffffffffu, u16 ? d[j] : d[j + 2], 16);
+        c = (u8 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, u8 ? b2[0] : b2[1], 8);
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) d[q] = __shfl_sync(0xffffffffu, c, ((q >> 1) & 1) * 16 + (q & 1) * 8);
+    } else {
+        static_assert(Q == 2, "warp_sums_x: Q = 2, 4 or 8");
+        const bool u16 = lane & 16;
+        c = (u16 ? d[1] : d[0]) + __shfl_xor_sync(0xffffffffu, u16 ? d[0] : d[1], 16);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) d[q] = __shfl_sync(0xffffffffu, c, q * 16);
+    }
+}
+
+// reg_apply for FP32 tiles of 2, 4 or 8 columns per warp: the dot products
+// and the updates two columns per instruction (ffma2), the column sums by
+// warp_sums_x.
+template <int R, int Q>
+__device__ __forceinline__ void reg_apply_f32x2(float (&a)[Q][R], const float (&vr)[R], const bool (&act)[R],
+                                                float tau, const float (&cm)[Q]) {
+    float2 dd[Q / 2];
+#pragma unroll
+    for (int p = 0; p < Q / 2; ++p) dd[p] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+        if (act[t]) {
+            const float2 vv = make_float2(vr[t], vr[t]);
+#pragma unroll
+            for (int p = 0; p < Q / 2; ++p) dd[p] = ffma2(vv, make_float2(a[2 * p][t], a[2 * p + 1][t]), dd[p]);
+        }
+    float d[Q];
+#pragma unroll
+    for (int p = 0; p < Q / 2; ++p) {
+        d[2 * p] = dd[p].x;
+        d[2 * p + 1] = dd[p].y;
+    }
+    warp_sums_x<Q>(d);
+    float2 ms[Q / 2];
+#pragma unroll
+    for (int p = 0; p < Q / 2; ++p) ms[p] = make_float2(-tau * d[2 * p] * cm[2 * p], -tau * d[2 * p + 1] * cm[2 * p + 1]);
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+        if (act[t]) {
+            const float2 vv = make_float2(vr[t], vr[t]);
+#pragma unroll
+            for (int p = 0; p < Q / 2; ++p) {
+                const float2 r = ffma2(ms[p], vv, make_float2(a[2 * p][t], a[2 * p + 1][t]));
+                a[2 * p][t] = r.x;
+                a[2 * p + 1][t] = r.y;
+            }
+        }
+}
+
 // x <- column q of a / column q of a <- x (q warp-uniform; one branch taken).
 template <typename T, int R, int Q>
 __device__ __forceinline__ void reg_col_get(const T (&a)[Q][R], int q, T (&x)[R]) {
@@ -279,7 +377,12 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
             for (int q = 0; q < Q; ++q)
                 if (q == q1) cm[q] = T(0);
         }
-        if (tk != T(0)) reg_apply<T, R, Q>(a, vr, act, tk, cm);
+        if (tk != T(0)) {
+            if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
+                reg_apply_f32x2<R, Q>(a, vr, act, tk, cm);
+            else
+                reg_apply<T, R, Q>(a, vr, act, tk, cm);
+        }
         if (k1 < nc && (k1 % NW) == warp) RTRACE(k, 3);
         reg_sync<NW, BAR>();
     }
@@ -303,7 +406,10 @@ __device__ void reg_apply_all(T (&m)[Q][R], const T *Vs, int ldv, const T *taus,
             act[t] = blk.active(t, k);
             vr[t] = act[t] ? Vs[(size_t)k * ldv + lane + 32 * t] : T(0);
         }
-        reg_apply<T, R, Q>(m, vr, act, tk, cm);
+        if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
+            reg_apply_f32x2<R, Q>(m, vr, act, tk, cm);
+        else
+            reg_apply<T, R, Q>(m, vr, act, tk, cm);
     }
 }
 
