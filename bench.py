@@ -5,7 +5,9 @@ Workload (default): n = 16384, mixed precision (FP32 data, tensor-core
 trailing update, FP64 Householder norms/tau/beta and FP64 Sturm recurrence),
 A = Q diag(D) Q^T with D geometrically spaced over 1e-6..1 in magnitude with
 random signs and 16-fold clusters of gap 1e-10, Q from the QR of a seeded
-N(0,1) matrix; first half-bandwidth b0 = 128, band schedule 128 -> 32 -> 16 -> 1.
+N(0,1) matrix; first half-bandwidth b0 = 128, band schedule from b0 down to 1
+chosen by the library's autotuner (sev_autotune, run once before the
+warm-up; --no-tune keeps the fixed rule 128 -> 32 -> 16 -> 1).
 A step is one sev_eigvalsh call (full-to-band, every band-to-band stage,
 bisection).  The FP64 form of the same matrix is timed beside it.
 
@@ -43,6 +45,8 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64-form timing")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
+    p.add_argument("--no-tune", action="store_true",
+                   help="run the library's fixed band schedule instead of autotuning it first")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return p.parse_args()
 
@@ -161,7 +165,7 @@ def schedule(b0, elem=4):
     return s
 
 
-def kernel_model(name, n, b0, elem):
+def kernel_model(name, n, b0, elem, sched=None):
     """Algorithmic work of one step for a kernel: (amount, unit, bound).
 
     syr2k / symm: 2 N^2 b flops per panel (lower triangle, both products).
@@ -175,7 +179,8 @@ def kernel_model(name, n, b0, elem):
     definition; each step is three FP64 instructions, division-free).
     """
     Ns = panel_sizes(n, b0)
-    sched = schedule(b0, elem)
+    if sched is None:
+        sched = schedule(b0, elem)
     if name in ("syr2k", "syr2k_tc"):
         flops = sum(2.0 * N * (N + 1) * b0 for N in Ns)
         return flops, "flop", "tensor" if name.endswith("_tc") else "alu"
@@ -475,7 +480,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_1604_03703_gb300 import api
+    from paper_1604_03703_gb300 import _lib, api
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -498,6 +503,21 @@ def run_ours(args):
     def barrier():
         if world > 1:
             dist.barrier()
+
+    # the band schedule: measured per stage at this order by the library's
+    # autotuner (untimed, once per process), for the fixed b0 and for a free b0
+    tune = None
+    if not args.no_tune:
+        t0 = time.perf_counter()
+        free_bands, free_pred = h.autotune(n, _lib.SEV_MIXED, 0)
+        t1 = time.perf_counter()
+        fixed_bands, fixed_pred = h.autotune(n, _lib.SEV_MIXED, b0)
+        t2 = time.perf_counter()
+        h.raise_device_error("autotune")
+        tune = {"b0_%d" % b0: {"schedule": fixed_bands, "predicted_ms": fixed_pred, "tuning_s": t2 - t1},
+                "free_b0": {"schedule": free_bands, "predicted_ms": free_pred, "tuning_s": t1 - t0}}
+    sched = h.eigvalsh_bands(n, b0, _lib.SEV_MIXED)
+    sched_free = h.eigvalsh_bands(n, 0, _lib.SEV_MIXED)
 
     # warm-up
     for _ in range(max(args.warmup, 3)):
@@ -544,7 +564,7 @@ def run_ours(args):
     lam_np = lam.cpu().numpy()
     err = float(np.abs(np.sort(lam_np) - D).max() / Dmax)
 
-    # the library's own default band width (b0 = 0 picks 64 at this size), same matrix
+    # the library's own choice of band width (b0 = 0: the tuned b0), same matrix
     auto = None
     if rank == 0 or world > 1:
         ea = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
@@ -559,7 +579,7 @@ def run_ours(args):
         h.raise_device_error("default b0")
         a_ms = min(e0.elapsed_time(e1) for e0, e1 in ea)
         a_err = float(np.abs(np.sort(lam.cpu().numpy()) - D).max() / Dmax)
-        auto = {"b0": 64, "schedule": schedule(64, 4), "ms_per_step": a_ms,
+        auto = {"b0": sched_free[0], "schedule": sched_free, "ms_per_step": a_ms,
                 "tflops": nominal_flops(n) / (a_ms / 1e3) / 1e12, "max_err_vs_D": a_err}
 
     # end to end through the host-buffer entry point (H2D + solve + D2H)
@@ -606,7 +626,7 @@ def run_ours(args):
         batched = bench_batched(h, device, args, rank, world)
 
     peaks = measured_peaks()
-    amount, unit, bound = kernel_model(dominant, n, b0, 4)
+    amount, unit, bound = kernel_model(dominant, n, b0, 4, sched)
     dom_ms_step = dom_ms / args.steps if dom_ms else prof[dominant][0]
     roof = roofline(dominant, amount, unit, bound, dom_ms_step, peaks, clk, 4)
     if roof is not None:
@@ -633,8 +653,8 @@ def run_ours(args):
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+bf16x3+f64", "data": "synthetic",
         "config": {"workload": "eigvalsh n=%d, A = Q diag(D) Q^T, D geometric 1e-6..1 with random signs and "
-                               "16-fold clusters (gap 1e-10), FP32 data, bands %s" % (n, "->".join(map(str, schedule(b0, 4)))),
-                   "n": n, "b0": b0, "schedule": schedule(b0, 4), "parallelism": "replicas" if world > 1 else "single",
+                               "16-fold clusters (gap 1e-10), FP32 data, bands %s" % (n, "->".join(map(str, sched))),
+                   "n": n, "b0": b0, "schedule": sched, "autotune": tune, "parallelism": "replicas" if world > 1 else "single",
                    "precision": "mixed: FP32 data and FP32 arithmetic, BF16x3 tensor-core trailing update "
                                 "(FP32 accumulation), pair-float Householder scalars, FP64 Sturm counts",
                    "l2": "inputs larger than L2 (1 GiB matrix per step); input restore excluded from step events"},

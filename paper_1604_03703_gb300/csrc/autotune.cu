@@ -207,12 +207,20 @@ static int autotune_t(sev_ctx *h, int n, int prec, int b0_req, TunedBands *out, 
             tune_fill_band_kernel<T><<<grid, 256, 0, h->stream>>>(nwarm, b, AB, ldab, 0x7A11ull);
             rc = w == 1 ? launch_band_tri<T>(h, nwarm, AB, ldab, b, ws, stage)
                         : launch_band_to_band<T>(h, nwarm, AB, ldab, b, w, ws, stage);
+            if (rc == SEV_ERR_UNSUPPORTED) {  // no kernel for this edge here: not a candidate
+                rc = SEV_OK;
+                continue;
+            }
             if (rc) break;
             tune_fill_band_kernel<T><<<grid, 256, 0, h->stream>>>(n, b, AB, ldab, 0x7A12ull + b * 131 + w);
             float ms = 0.f;
             rc = time_ms(h, [&] { return w == 1 ? launch_band_tri<T>(h, n, AB, ldab, b, ws, stage)
                                                  : launch_band_to_band<T>(h, n, AB, ldab, b, w, ws, stage); },
                          &ms);
+            if (rc == SEV_ERR_UNSUPPORTED) {
+                rc = SEV_OK;
+                continue;
+            }
             cost[wlog(b)][wlog(w)] = ms;
         }
     }
@@ -239,10 +247,18 @@ static int autotune_t(sev_ctx *h, int n, int prec, int b0_req, TunedBands *out, 
         const int nw = 2 * b0 + 2 < n ? 2 * b0 + 2 : n;  // warm-up order: a couple of panels
         tune_fill_sym_kernel<T><<<grid, 256, 0, h->stream>>>(nw, A, nw, 0xF00Dull);
         rc = launch_full_to_band<T>(h, nw, A, nw, b0, AB, ldab, ws, stage);
+        if (rc == SEV_ERR_UNSUPPORTED) {  // this width has no full-to-band kernel here
+            rc = SEV_OK;
+            continue;
+        }
         if (rc) break;
         tune_fill_sym_kernel<T><<<grid, 256, 0, h->stream>>>(n, A, n, 0xF00Eull + b0);
         float ms = 0.f;
         rc = time_ms(h, [&] { return launch_full_to_band<T>(h, n, A, n, b0, AB, ldab, ws, stage); }, &ms);
+        if (rc == SEV_ERR_UNSUPPORTED) {
+            rc = SEV_OK;
+            continue;
+        }
         const double tot = ms + best[l];
         if (!rc && (tot_best < 0.0 || tot < tot_best)) {
             tot_best = tot;

@@ -490,3 +490,26 @@ def test_autotune_choice_is_the_schedule_run(torch_cuda, orc, tmp_path, monkeypa
     h2 = api.Handle(0)
     assert h2.eigvalsh_bands(n, 128, _lib.SEV_MIXED) == b128
     h2.close()
+
+
+@pytest.mark.gpu
+def test_autotune_fp64_skips_unsupported_widths(torch_cuda, tmp_path, monkeypatch):
+    """In FP64 some widths have no kernel on this GPU (the b0 = 128 panel
+    does not fit shared memory); the autotuner leaves them out instead of
+    failing, and the FP64 eigensolve then runs the tuned path."""
+    torch = torch_cuda
+    from paper_1604_03703_gb300 import _lib, api
+
+    monkeypatch.setenv("SEV_TUNE_CACHE", str(tmp_path / "tune.txt"))
+    h = api.Handle(0)
+    n = 700
+    bands, ms = h.autotune(n, _lib.SEV_FP64, 0)
+    h.raise_device_error("autotune")
+    assert bands[0] in (32, 64) and bands[-1] == 1 and ms > 0, bands
+    assert h.eigvalsh_bands(n, 0, _lib.SEV_FP64) == bands
+    A = I.semicircle(n, 9501)
+    got = h.eigvalsh(dev(torch, A, torch.float64), 0).cpu().numpy()
+    h.raise_device_error()
+    lam = np.linalg.eigvalsh(A)
+    assert np.abs(got - lam).max() <= 1e-11 * np.abs(lam).max()
+    h.close()
