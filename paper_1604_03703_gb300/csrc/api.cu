@@ -297,6 +297,7 @@ int sev_create(sev_handle *handle, int device) {
         return SEV_ERR_CUDA;
     }
     if (const char *v = getenv("SEV_LEAF_ROWS")) h->leaf_rows_override = atoi(v);
+    if (const char *v = getenv("SEV_CHASE_X3_MIN_B")) h->chase_x3_min_b = atoi(v);
     tune_cache_load(h);
     *handle = h;
     return SEV_OK;

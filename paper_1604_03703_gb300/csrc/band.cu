@@ -384,6 +384,293 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
     BTRACE(5);
 }
 
+// ------------------------------------------------ three-CTA cluster chase
+// The same chase split over a cluster of three CTAs, for wide bands where
+// one chase is long and only ~J/3 sweeps can progress at once (most SMs
+// would idle): rank 0 factorises the qr block and updates the diagonal
+// block X_d; rank 1 updates the rows above the qr rows and rank 2 the rows
+// below (the one-sided X <- X - (X U T) U^T of each), each from its own
+// copy of U and U T, read from rank 0's shared memory once rank 0 has
+// formed them.  Ranks 1 and 2 load their blocks while rank 0 runs the QR.
+// Two cluster barriers per chase: A (U, U T and nr ready on rank 0) and B
+// (every write of the chase done; the next chase may start).
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync() {
+    cluster_arrive();
+    cluster_wait();
+}
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// Generic address of the same shared variable in CTA `rank` of the cluster.
+template <typename P>
+__device__ __forceinline__ P *cluster_map(P *p, unsigned rank) {
+    unsigned long long out;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(out) : "l"((unsigned long long)p), "r"(rank));
+    return (P *)out;
+}
+
+// One-sided update of one row block (rows x n_r, X[a + c ldb1], row a of
+// the block <-> band position (row0 + a) for rank 2 or column (col0 + a) for
+// rank 1): W = X (U T); X <- X - W U^T; written back.
+template <typename T>
+__device__ void chase_rows_update(T *AB, int ldab, int n, int rows, int n_r, int nr, int o_qr_r, int base, bool above,
+                                  ChaseSmem<T> &S, int &bad) {
+    const int ldb1 = S.ldb1, tid = threadIdx.x, nt = blockDim.x;
+    constexpr bool kVec = sizeof(T) == 4;
+    T *X = S.Xs;
+    cta_mm<T, 4, 4, false, kVec>(rows, nr, n_r, T(1), X, ldb1, S.UTs, ldb1, 0, nullptr, 0, nullptr, 0, T(0), S.Ws,
+                                 ldb1);
+    __syncthreads();
+    const bool tiled = n_r >= 64;
+    if (tiled) {
+        cta_mm<T, 8, 8, true, kVec>(rows, n_r, nr, T(-1), S.Ws, ldb1, S.Us, ldb1, 0, nullptr, 0, nullptr, 0, T(1), X,
+                                    ldb1);
+        __syncthreads();
+    }
+    auto updated = [&](int r, int c) {
+        T v = X[r + (size_t)c * ldb1];
+        if (!tiled)
+            for (int m = 0; m < nr; ++m) v -= S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
+        return v;
+    };
+    if (above) {
+        for (int idx = tid; idx < rows * n_r; idx += nt) {
+            const int c = idx % n_r, r = idx / n_r;
+            bst(AB, ldab, n, o_qr_r + c, base + r, updated(r, c), bad);
+        }
+    } else {
+        for (int idx = tid; idx < rows * n_r; idx += nt) {
+            const int r = idx % rows, c = idx / rows;
+            bst(AB, ldab, n, base + r, o_qr_r + c, updated(r, c), bad);
+        }
+    }
+}
+
+// Rank `rank`'s share of chase (i, j).  *nr_r0 is rank 0's count of
+// reflectors (shared-memory variable of rank 0, mapped).  Every rank passes
+// cluster barrier A exactly once.
+template <typename T, int RQ, int QQ>
+__device__ void band_chase_x3(T *AB, int ldab, int n, int b, int h, int i, int j, ChaseSmem<T> &S, unsigned rank,
+                              int *s_nr, int &bad) {
+    const int o_qr_r = (i - 1) * h + (j - 1) * b + h;
+    int o_qr_c, o_v, o_up_c, lim;
+    if (j == 1) {
+        o_qr_c = o_qr_r - h;
+        o_v = 0;
+        o_up_c = o_qr_r;
+        lim = 2 * b;
+    } else {
+        o_qr_c = o_qr_r - b;
+        o_v = b - h;
+        o_up_c = o_qr_c + h;
+        lim = 3 * b - h;
+    }
+    const int n_r = min(n - o_qr_r, b);
+    const int n_c = min(n - o_up_c, lim);
+    const int ldb1 = S.ldb1, ldh1 = S.ldh1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr bool kVec = sizeof(T) == 4;
+
+    if (rank != 0) {
+        // the row block of this rank, loaded while rank 0 factorises
+        const bool above = rank == 1;
+        const int a0 = above ? 0 : o_v + n_r, rows = above ? o_v : n_c - (o_v + n_r);
+        if (rows > 0) {
+            if (above) {
+                // element (qr row c, column o_up_c + a) is stored as (row, col) = (o_qr_r + c, o_up_c + a)
+                batched_copy<T>(
+                    rows * n_r, tid, nt, [&](int k) { return bld(AB, ldab, n, o_qr_r + k % n_r, o_up_c + k / n_r, bad); },
+                    [&](int k, T v) { S.Xs[k / n_r + (size_t)(k % n_r) * ldb1] = v; });
+            } else {
+                batched_copy<T>(
+                    rows * n_r, tid, nt,
+                    [&](int k) { return bld(AB, ldab, n, o_up_c + a0 + k % rows, o_qr_r + k / rows, bad); },
+                    [&](int k, T v) { S.Xs[k % rows + (size_t)(k / rows) * ldb1] = v; });
+            }
+        }
+        cluster_sync();  // A
+        int *nr0 = cluster_map(s_nr, 0);
+        const int nr = *(volatile int *)nr0;
+        if (rows <= 0 || nr <= 0) return;
+        // U and U T from rank 0 (whole padded columns, 16-byte pieces)
+        const float4 *src = (const float4 *)cluster_map(S.Us, 0);
+        float4 *dst = (float4 *)S.Us;
+        const int q_u = (int)(((size_t)ldb1 * nr * sizeof(T)) / 16);  // Us and UTs: columns of ldb1
+        const int q_off = (int)(((size_t)ldb1 * h * sizeof(T)) / 16);  // UTs = Us + ldb1 h
+        for (int q = tid; q < 2 * q_u; q += nt) {
+            const int at = q < q_u ? q : q_off + (q - q_u);
+            dst[at] = src[at];
+        }
+        __syncthreads();
+        chase_rows_update<T>(AB, ldab, n, rows, n_r, nr, o_qr_r, o_up_c + a0, above, S, bad);
+        return;
+    }
+
+    // ---- rank 0: QR of the n_r x h block, U, T, U T; then X_d
+    const int warp = tid >> 5, lane = tid & 31;
+    int nr = n_r - 1 < h ? n_r - 1 : h;
+    if (nr < 0) nr = 0;
+    if (warp < 4) {
+        T a[QQ][RQ];
+#pragma unroll
+        for (int q = 0; q < QQ; ++q)
+#pragma unroll
+            for (int t = 0; t < RQ; ++t) {
+                const int r = lane + 32 * t, c = warp + 4 * q;
+                a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
+            }
+        reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau);
+#pragma unroll
+        for (int q = 0; q < QQ; ++q)
+#pragma unroll
+            for (int t = 0; t < RQ; ++t) {
+                const int r = lane + 32 * t, c = warp + 4 * q;
+                if (r < n_r && c < h) {
+                    bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, r <= c ? a[q][t] : T(0), bad);
+                    if (c < nr) S.Us[r + (size_t)c * ldb1] = r < c ? T(0) : (r == c ? T(1) : a[q][t]);
+                }
+            }
+    } else if (nr > 0) {
+        // warps 4-7 meanwhile: the diagonal block (lower triangle, mirrored)
+        const int t4 = tid - 128;
+        batched_copy<T>(
+            n_r * n_r, t4, 128,
+            [&](int k) {
+                const int r = k % n_r, c = k / n_r;
+                return r >= c ? bld(AB, ldab, n, o_qr_r + r, o_qr_r + c, bad) : T(0);
+            },
+            [&](int k, T v) {
+                const int r = k % n_r, c = k / n_r;
+                if (r >= c) S.Xs[r + (size_t)c * ldb1] = v;
+            });
+        asm volatile("bar.sync 2, 128;" ::: "memory");
+        for (int idx = t4; idx < n_r * n_r; idx += 128) {
+            const int r = idx % n_r, c = idx / n_r;
+            if (r < c) S.Xs[r + (size_t)c * ldb1] = S.Xs[c + (size_t)r * ldb1];
+        }
+    }
+    if (tid == 0) *s_nr = nr;
+    __syncthreads();
+    if (nr > 0) {
+        if (nr <= 32) {
+            cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Us, ldb1, T(0), S.Zs, ldh1);
+            __syncthreads();
+            form_t_from_g(nr, S.Zs, ldh1, S.tau, S.Ts, ldh1);
+        } else {
+            cta_form_t(n_r, nr, S.Us, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
+        }
+        cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, 0, nullptr, 0, nullptr, 0, T(0),
+                                     S.UTs, ldb1);
+    }
+    cluster_sync();  // A: U, U T and nr are ready for ranks 1 and 2
+    if (nr == 0) return;
+    // W_d = X_d (U T); S = U^T W_d; Z = T^T S; V_d = -W_d + 1/2 U Z
+    cta_mm<T, 4, 4, false, kVec>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, 0, nullptr, 0, nullptr, 0, T(0), S.Ws,
+                                 ldb1);
+    __syncthreads();
+    cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Ws, ldb1, T(0), S.Zs, ldh1);
+    __syncthreads();
+    for (int c = tid; c < nr; c += nt) {
+        for (int a = nr - 1; a >= 0; --a) {
+            T s = 0;
+            for (int q = 0; q <= a; ++q) s += S.Ts[q + (size_t)a * ldh1] * S.Zs[q + (size_t)c * ldh1];
+            S.Zs[a + (size_t)c * ldh1] = s;
+        }
+    }
+    __syncthreads();
+    cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, 0, nullptr, 0, nullptr, 0, T(-1), S.Ws,
+                                 ldb1);
+    __syncthreads();
+    if (n_r >= 64) {
+        cta_mm<T, 8, 8, true, kVec>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, nr, S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs,
+                                    ldb1);
+        __syncthreads();
+        for (int idx = tid; idx < n_r * n_r; idx += nt) {
+            const int r = idx % n_r, c = idx / n_r;
+            if (r < c) continue;
+            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
+        }
+    } else {
+        for (int idx = tid; idx < n_r * n_r; idx += nt) {
+            const int r = idx % n_r, c = idx / n_r;
+            if (r < c) continue;
+            T s = 0;
+            for (int m = 0; m < nr; ++m)
+                s += S.Us[r + (size_t)m * ldb1] * S.Ws[c + (size_t)m * ldb1] +
+                     S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
+            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
+        }
+    }
+}
+
+// Capped wait of one thread until sweep s - 1 has completed `need` chases;
+// false on expiry or a latched error (then the error word is set).
+__device__ __forceinline__ bool wait_progress(const int *progress, int s, int need, int *err) {
+    const long long t0 = clock64();
+    while (ld_acquire(&progress[s - 1]) < need) {
+        if (*(volatile int *)err != 0) return false;
+        if (wait_expired(t0, err)) {
+            latch_error(err, SEV_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Cluster of three CTAs per sweep.  Rank 0 takes sweeps from the counter
+// and hands the index to ranks 1 and 2 through its shared memory.  Every
+// rank's thread 0 waits for the previous sweep itself (before barrier B of
+// the preceding chase); a rank whose wait fails raises rank 0's abort flag,
+// which every rank reads after the same barrier, so all three leave
+// together, after one more barrier (no CTA exits while a peer may still
+// read its shared memory).
+template <typename T, int RQ, int QQ>
+__global__ void __cluster_dims__(3, 1, 1) __launch_bounds__(kThreads)
+    band_chase_x3_kernel(int n, T *AB, int ldab, int b, int h, int nsweeps, int *progress, int *sweep_ctr, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    ChaseSmem<T> S(smem, b, h);
+    __shared__ int s_sweep, s_abort, s_nr;
+    const unsigned rank = cluster_rank();
+    int bad = 0;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        s_nr = 0;
+    }
+    int *abort0 = cluster_map(&s_abort, 0);
+    int *sweep0 = cluster_map(&s_sweep, 0);
+    cluster_sync();  // rank 0's flags are initialised before any rank may raise them
+    for (;;) {
+        if (rank == 0 && threadIdx.x == 0) s_sweep = atomicAdd(sweep_ctr, 1);
+        cluster_sync();  // C: the sweep index is published
+        const int s = *(volatile int *)sweep0;
+        if (s >= nsweeps) break;
+        const int i = s + 1;
+        const int J = band_num_chases(n, b, h, i);
+        const int Jprev = i > 1 ? band_num_chases(n, b, h, i - 1) : 0;
+        if (i > 1 && threadIdx.x == 0 && !wait_progress(progress, s, min(3, Jprev), err)) atomicOr(abort0, 1);
+        cluster_sync();  // B of "chase 0": every rank may start chase 1
+        if (*(volatile int *)abort0) break;
+        for (int j = 1; j <= J; ++j) {
+            band_chase_x3<T, RQ, QQ>(AB, ldab, n, b, h, i, j, S, rank, &s_nr, bad);
+            __syncthreads();
+            if (i > 1 && j < J && threadIdx.x == 0 && !wait_progress(progress, s, min(j + 3, Jprev), err))
+                atomicOr(abort0, 1);
+            cluster_sync();  // B: chase j is complete on all ranks
+            // the release store orders the cluster's writes (made visible to
+            // rank 0's thread 0 by the barrier) before the progress flag
+            if (rank == 0 && threadIdx.x == 0) st_release(&progress[s], j);
+            if (*(volatile int *)abort0) break;
+        }
+        if (*(volatile int *)abort0) break;
+    }
+    cluster_sync();  // no rank leaves while a peer may still read its shared memory
+    if (__syncthreads_or(bad) && threadIdx.x == 0) latch_error(err, SEV_ERR_INTERNAL);
+}
+
 template <typename T, int RQ, int QQ>
 __global__ void __launch_bounds__(kThreads) band_chase_kernel(int n, T *AB, int ldab, int b, int h, int nsweeps,
                                                                int *progress, int *sweep_ctr, int *err) {
@@ -440,6 +727,44 @@ size_t band_workspace(int n, int b, int h) {
     return c.bytes();
 }
 
+// The cluster chase for tile (RQ, QQ); SEV_ERR_UNSUPPORTED when no cluster
+// of three such CTAs fits on the GPU (the caller then runs one CTA a sweep).
+template <typename T>
+static int launch_chase_x3(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, int nsweeps, int *progress, int *ctr,
+                           int RQ, int QQ) {
+    void (*kern)(int, T *, int, int, int, int, int *, int *, int *) = nullptr;
+    if (RQ == 2 && QQ == 1) kern = band_chase_x3_kernel<T, 2, 1>;
+    if (RQ == 2 && QQ == 2) kern = band_chase_x3_kernel<T, 2, 2>;
+    if (RQ == 2 && QQ == 4) kern = band_chase_x3_kernel<T, 2, 4>;
+    if (RQ == 2 && QQ == 8) kern = band_chase_x3_kernel<T, 2, 8>;
+    if (RQ == 4 && QQ == 1) kern = band_chase_x3_kernel<T, 4, 1>;
+    if (RQ == 4 && QQ == 2) kern = band_chase_x3_kernel<T, 4, 2>;
+    if (RQ == 4 && QQ == 4) kern = band_chase_x3_kernel<T, 4, 4>;
+    if (RQ == 4 && QQ == 8) kern = band_chase_x3_kernel<T, 4, 8>;
+    if (RQ == 4 && QQ == 16) kern = band_chase_x3_kernel<T, 4, 16>;
+    if (!kern) return SEV_ERR_UNSUPPORTED;
+    const size_t smem = band_smem_bytes<T>(b, h);
+    if (smem > hd->smem_optin) return SEV_ERR_UNSUPPORTED;
+    SEV_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int busy = band_num_chases(n, b, h, 0) / 3 + 8;
+    int clusters = busy < nsweeps ? busy : nsweeps;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(3 * clusters);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = hd->stream;
+    int fit = 0;
+    if (cudaOccupancyMaxActiveClusters(&fit, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return SEV_ERR_UNSUPPORTED;
+    }
+    if (fit < 1) return SEV_ERR_UNSUPPORTED;
+    if (clusters > fit) clusters = fit;
+    SEV_LAUNCH(hd, K_BAND_CHASE, kern, 3 * clusters, kThreads, smem, n, AB, ldab, b, h, nsweeps, progress, ctr,
+               hd->d_err);
+    return SEV_OK;
+}
+
 template <typename T>
 int launch_band_to_band(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, void *ws, size_t ws_bytes) {
     const int nsweeps = band_num_sweeps(n, h);
@@ -454,6 +779,11 @@ int launch_band_to_band(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, void 
     SEV_CUDA(cudaMemsetAsync(ctr, 0, sizeof(int), hd->stream));
     // register path when its tile and its second block buffer fit
     const int RQ = chase_tile_r(b), QQ = chase_tile_q(h);
+    // wide bands: the three-CTA cluster chase when a cluster fits
+    if (RQ > 0 && QQ > 0 && b >= hd->chase_x3_min_b) {
+        int rc = launch_chase_x3<T>(hd, n, AB, ldab, b, h, nsweeps, progress, ctr, RQ, QQ);
+        if (rc != SEV_ERR_UNSUPPORTED) return rc;
+    }
     auto kern = band_chase_kernel<T, 0, 0>;
     if (RQ > 0 && QQ > 0 && band_smem_reg<T>(b, h) <= hd->smem_optin) {
         smem = band_smem_reg<T>(b, h);

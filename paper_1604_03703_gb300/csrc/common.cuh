@@ -74,6 +74,7 @@ struct sev_ctx {
     size_t h_stage_bytes = 0;
     unsigned long long timing = 0;  // bit k: time kernel id k
     int leaf_rows_override = 0;  // SEV_LEAF_ROWS: rows per tree-QR leaf (tests)
+    int chase_x3_min_b = 64;     // SEV_CHASE_X3_MIN_B: narrowest band chased by three-CTA clusters
     int batch_b_fp64 = 0;        // band width chosen by sev_batch_autotune (0: default)
     int batch_b_mixed = 0;
     std::vector<sev::TunedBands> tuned;  // sev_autotune results

@@ -119,7 +119,9 @@ def test_bisect_clusters_and_zeros(H, torch_cuda, orc):
 BAND_CASES = [(200, 8, 4), (203, 16, 8), (150, 6, 3), (161, 32, 16), (97, 4, 1), (130, 8, 2), (64, 2, 1), (5, 2, 1),
               (40, 32, 16),
               # b -> 1 in one stage (sliding-window kernel): several sweep groups, ragged ends
-              (300, 16, 1), (333, 32, 1), (211, 8, 1), (3, 2, 1), (4, 2, 1), (37, 32, 1), (130, 6, 1)]
+              (300, 16, 1), (333, 32, 1), (211, 8, 1), (3, 2, 1), (4, 2, 1), (37, 32, 1), (130, 6, 1),
+              # wide bands (three-CTA cluster chase), ragged ends
+              (301, 64, 16), (263, 64, 32)]
 
 
 @pytest.mark.parametrize("n,b,h", BAND_CASES)
@@ -138,7 +140,8 @@ def test_band_to_band_fp64_vs_oracle(H, torch_cuda, orc, n, b, h):
     assert np.all(got[np.abs(i - j) > h] == 0.0)
 
 
-@pytest.mark.parametrize("n,b,h", [(300, 16, 8), (257, 64, 32), (411, 128, 64), (200, 8, 4), (500, 32, 1), (280, 16, 1)])
+@pytest.mark.parametrize("n,b,h", [(300, 16, 8), (257, 64, 32), (411, 128, 64), (200, 8, 4), (500, 32, 1), (280, 16, 1),
+                                   (601, 128, 32), (389, 128, 8)])
 def test_band_to_band_fp32_vs_oracle(H, torch_cuda, orc, n, b, h):
     torch = torch_cuda
     A = I.random_band(n, b, 7100 + n + b)
@@ -153,6 +156,29 @@ def test_band_to_band_fp32_vs_oracle(H, torch_cuda, orc, n, b, h):
     assert np.abs(np.tril(got) - np.tril(ref)).max() <= 20 * n * eps32 * scale
     lam = np.linalg.eigvalsh(A)
     assert np.abs(np.linalg.eigvalsh(got) - lam).max() <= 1e-5 * np.abs(lam).max()
+
+
+@pytest.mark.parametrize("n,b,h,dt", [(700, 128, 32, "f32"), (517, 128, 16, "f32"), (450, 64, 16, "f64"),
+                                      (333, 64, 32, "f32")])
+def test_band_chase_cluster_matches_single_cta(torch_cuda, monkeypatch, n, b, h, dt):
+    """The three-CTA cluster chase (wide bands) splits each chase over three
+    CTAs but keeps every entry's arithmetic: it reproduces the one-CTA chase
+    bit for bit."""
+    torch = torch_cuda
+    from paper_1604_03703_gb300 import api
+
+    dtype = torch.float32 if dt == "f32" else torch.float64
+    A = I.random_band(n, b, 7300 + n + b + h)
+    outs = []
+    for min_b in ("64", "100000"):  # cluster chase on / off
+        monkeypatch.setenv("SEV_CHASE_X3_MIN_B", min_b)
+        hd = api.Handle(0)
+        AB = to_band_tensor(torch, A, 2 * b, dtype)
+        hd.band_to_band(AB, b, h)
+        hd.raise_device_error()
+        outs.append(AB.cpu().numpy())
+        hd.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
 
 
 # -------------------------------------------------------------- full-to-band
