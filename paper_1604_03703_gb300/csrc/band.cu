@@ -82,12 +82,9 @@ __device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, i
     AB[d + (size_t)c * ldab] = v;
 }
 // Shared memory of one chase: U, U T, the block X being updated, W, T, a
-// small product Z, tau, the double-buffered reflector of the register QR and
-// a reduction scratch.
-// Shared memory of one chase: U, U T, the block X being updated, W, T, a
-// small product Z, tau, the double-buffered reflector of the register QR, a
-// reduction scratch and (register path) a second block buffer Xb for the
-// rows above the qr rows, loaded while the QR runs.
+// small product Z, tau, the three reflector buffers of the register QR, a
+// reduction scratch and (one-CTA register path) a second block buffer Xb for
+// the rows above the qr rows, loaded while the QR runs.
 template <typename T>
 struct ChaseSmem {
     T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau, *vs, *Xb;
@@ -104,7 +101,7 @@ struct ChaseSmem {
         Zs = Ts + (size_t)ldh1 * h;
         tau = Zs + (size_t)ldh1 * h;
         vs = tau + h;
-        size_t off = (size_t)((unsigned char *)(vs + 2 * 128) - base);
+        size_t off = (size_t)((unsigned char *)(vs + 3 * 128) - base);
         off = (off + 15) & ~(size_t)15;
         red = (double *)(base + off);
         Xb = (T *)(base + off + 32 * sizeof(double));
@@ -121,7 +118,7 @@ __host__ __device__ constexpr int chase_tile_q(int h) {
 template <typename T>
 static size_t band_smem_base(int b, int h) {
     const size_t ldb1 = b + 4, ldh1 = h + 1;
-    size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h + 2 * 128;
+    size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h + 3 * 128;
     size_t bytes = e * sizeof(T);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + 32 * sizeof(double);
@@ -733,6 +730,9 @@ template <typename T>
 static int launch_chase_x3(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, int nsweeps, int *progress, int *ctr,
                            int RQ, int QQ) {
     void (*kern)(int, T *, int, int, int, int, int *, int *, int *) = nullptr;
+    if (RQ == 1 && QQ == 1) kern = band_chase_x3_kernel<T, 1, 1>;
+    if (RQ == 1 && QQ == 2) kern = band_chase_x3_kernel<T, 1, 2>;
+    if (RQ == 1 && QQ == 4) kern = band_chase_x3_kernel<T, 1, 4>;
     if (RQ == 2 && QQ == 1) kern = band_chase_x3_kernel<T, 2, 1>;
     if (RQ == 2 && QQ == 2) kern = band_chase_x3_kernel<T, 2, 2>;
     if (RQ == 2 && QQ == 4) kern = band_chase_x3_kernel<T, 2, 4>;

@@ -55,7 +55,7 @@ template <typename T, int R, int Q>
 __global__ void __launch_bounds__(kRegThreads, 1)
     rtsqr_leaf_qr_kernel(const T *__restrict__ P, int ldp, int N, int b, int L, T *__restrict__ Y, int ldy,
                          T *__restrict__ tau, int *__restrict__ nref, T *__restrict__ Rbuf) {
-    __shared__ __align__(16) T vs[2 * 32 * R];
+    __shared__ __align__(16) T vs[3 * 32 * R];
     __shared__ T taus[kRegWarps * Q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int l = blockIdx.x;
@@ -94,7 +94,7 @@ template <typename T, int R, int Q>
 __global__ void __launch_bounds__(kRegThreads, 1)
     rtsqr_node_qr_kernel(int b, int cnt_child, int off_child, int off_node, T *__restrict__ Rbuf,
                          T *__restrict__ Ylev, size_t ystride, T *__restrict__ tau, int *__restrict__ nref) {
-    __shared__ __align__(16) T vs[2 * 32 * R];
+    __shared__ __align__(16) T vs[3 * 32 * R];
     __shared__ T taus[kRegWarps * Q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x;

@@ -310,10 +310,21 @@ __device__ __forceinline__ T reg_house(T (&x)[R], int k, T *vout) {
     return tau;
 }
 
-// Householder QR of the m x nc block held in `a` (m <= 32R, nc <= 16Q; rows
-// >= m and columns >= nc zero), r = min(nc, m - 1) reflectors.  On return
-// column c holds R above and on the diagonal and v_c below it (unit
-// diagonal implicit); taus[c] = tau_c.  vs: 2 x 32R shared scratch.
+// Householder QR of the m x nc block held in `a` (m <= 32R, nc <= NW Q;
+// rows >= m and columns >= nc zero), r = min(nc, m - 1) reflectors.  On
+// return column c holds R above and on the diagonal and v_c below it (unit
+// diagonal implicit); taus[c] = tau_c.  vs: 3 x 32R shared scratch.
+//
+// Step k applies reflector k.  The warp owning column k + 1 first brings
+// that column up to date and forms reflector k + 1 from it (lookahead); it
+// leaves its other columns for the next step, where it applies reflectors
+// k and k + 1 to them back to back while the next owner forms reflector
+// k + 2.  So a step lasts one column update plus one reflector, the owner's
+// share of the trailing update being off the critical path; every column
+// still receives the reflectors in order 0, 1, 2, ... (the same arithmetic
+// as applying them one step at a time).  Reflectors rotate through three
+// buffers: the deferred warp still reads reflector k - 1 in step k while
+// the owner writes k + 1.
 // Barrier of the warps running reg_qr: the whole CTA (BAR = 0) or named
 // barrier BAR over warps 0 .. NW-1 (the rest of the CTA does other work).
 template <int NW, int BAR>
@@ -324,8 +335,37 @@ __device__ __forceinline__ void reg_sync() {
         asm volatile("bar.sync %0, %1;" ::"n"(BAR), "n"(NW * 32) : "memory");
 }
 
+// The reflector in buffer slot k % 3, restricted to the row blocks it can
+// touch, applied to this warp's columns c with lo < c < nc.
+template <typename T, int R, int Q, int NW>
+__device__ __forceinline__ void reg_apply_step(T (&a)[Q][R], const RowBlocks<R> &blk, const T *vs, const T *taus,
+                                               int k, int lo, int nc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const T tk = taus[k];
+    if (tk == T(0)) return;
+    const T *v = vs + (k % 3) * (32 * R);
+    bool act[R];
+    T vr[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        act[t] = blk.active(t, k);
+        vr[t] = act[t] ? v[lane + 32 * t] : T(0);
+    }
+    T cm[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int c = warp + NW * q;
+        cm[q] = (c > lo && c < nc) ? T(1) : T(0);
+    }
+    if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
+        reg_apply_f32x2<R, Q>(a, vr, act, tk, cm);
+    else
+        reg_apply<T, R, Q>(a, vr, act, tk, cm);
+}
+
 template <typename T, int R, int Q, int NW, int BAR = 0>
 __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
+    static_assert(NW >= 2, "reg_qr: the owner of a column and of the next one must differ");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = nc < m - 1 ? nc : m - 1;
     if (r <= 0) {
@@ -338,27 +378,24 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
         if (lane == 0) taus[0] = t0;
     }
     reg_sync<NW, BAR>();
-    for (int k = 0; k < r; ++k) {
-        const T *v = vs + (k & 1) * (32 * R);
-        const T tk = taus[k];
-        bool act[R];
-        T vr[R];
-#pragma unroll
-        for (int t = 0; t < R; ++t) {
-            act[t] = blk.active(t, k);
-            vr[t] = act[t] ? v[lane + 32 * t] : T(0);
-        }
-        T cm[Q];
-#pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            const int c = warp + NW * q;
-            cm[q] = (c > k && c < nc) ? T(1) : T(0);
-        }
+    // k = r: no step, only the last owner's deferred share (reflector r - 1
+    // on its columns past r)
+    for (int k = 0; k <= r; ++k) {
         const int k1 = k + 1;
-        if (warp == 0) RTRACE(k, 0);
-        if (k1 < nc && (k1 % NW) == warp) {
-            // lookahead: column k+1 first (taken out of the tile, so the
-            // reflector code is emitted once), then reflector k+1 from it
+        const bool step = k < r;
+        if (warp == 0 && step) RTRACE(k, 0);
+        if (step && k1 < nc && (k1 % NW) == warp) {
+            // owner of column k + 1: that column only (taken out of the tile,
+            // so the reflector code is emitted once), then reflector k + 1
+            const T tk = taus[k];
+            const T *v = vs + (k % 3) * (32 * R);
+            bool act[R];
+            T vr[R];
+#pragma unroll
+            for (int t = 0; t < R; ++t) {
+                act[t] = blk.active(t, k);
+                vr[t] = act[t] ? v[lane + 32 * t] : T(0);
+            }
             const int q1 = k1 / NW;
             T x[1][R];
             reg_col_get<T, R, Q>(a, q1, x[0]);
@@ -368,23 +405,23 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
             }
             RTRACE(k, 1);
             if (k1 < r) {
-                const T t1 = reg_house<T, R>(x[0], k1, vs + (k1 & 1) * (32 * R));
+                const T t1 = reg_house<T, R>(x[0], k1, vs + (k1 % 3) * (32 * R));
                 if (lane == 0) taus[k1] = t1;
             }
             RTRACE(k, 2);
             reg_col_put<T, R, Q>(a, q1, x[0]);
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                if (q == q1) cm[q] = T(0);
+        } else {
+            // the previous owner (column k is its own) catches up on
+            // reflector k - 1 first (column k already has it); one loop, so
+            // the update code is emitted once
+            const bool deferred = k >= 1 && k < nc && (k % NW) == warp;
+            const int kend = step ? k : k - 1;
+            for (int kk = deferred ? k - 1 : k; kk <= kend; ++kk) reg_apply_step<T, R, Q, NW>(a, blk, vs, taus, kk, k, nc);
         }
-        if (tk != T(0)) {
-            if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
-                reg_apply_f32x2<R, Q>(a, vr, act, tk, cm);
-            else
-                reg_apply<T, R, Q>(a, vr, act, tk, cm);
+        if (step) {
+            if (k1 < nc && (k1 % NW) == warp) RTRACE(k, 3);
+            reg_sync<NW, BAR>();
         }
-        if (k1 < nc && (k1 % NW) == warp) RTRACE(k, 3);
-        reg_sync<NW, BAR>();
     }
     return r;
 }
