@@ -46,7 +46,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-batched", action="store_true", help="skip the batched workloads")
     p.add_argument("--no-tune", action="store_true",
-                   help="run the library's fixed band schedule instead of autotuning it first")
+                   help="skip the autotuning call: the library's own schedule (a tuned one from SEV_TUNE_CACHE, "
+                        "else the fixed rule)")
+    p.add_argument("--no-free-b0", action="store_true", help="skip the comparison run at the library's own b0")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return p.parse_args()
 
@@ -566,7 +568,7 @@ def run_ours(args):
 
     # the library's own choice of band width (b0 = 0: the tuned b0), same matrix
     auto = None
-    if rank == 0 or world > 1:
+    if not args.no_free_b0:
         ea = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
         A.copy_(A0)
         h.eigvalsh(A, 0, out=lam)

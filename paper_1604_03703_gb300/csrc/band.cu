@@ -35,9 +35,17 @@ extern "C" int sev_trace_set_band(void *p) {
     do {                                                                       \
         if (threadIdx.x == 0 && sev_btrace && i == 40 && j == 20) sev_btrace[k] = clock64(); \
     } while (0)
+// cluster chase: slot k of rank r at 16 + 16 r (each rank's own SM clock)
+#define BTRACE3(k)                                                                            \
+    do {                                                                                      \
+        if (threadIdx.x == 0 && sev_btrace && i == 40 && j == 20) sev_btrace[16 + 16 * rank + (k)] = clock64(); \
+    } while (0)
 #else
 #define BTRACE(k) \
     do {          \
+    } while (0)
+#define BTRACE3(k) \
+    do {           \
     } while (0)
 #endif
 
@@ -87,7 +95,7 @@ __device__ __forceinline__ void bst(T *AB, int ldab, int n, int r, int c, T v, i
 // the rows above the qr rows, loaded while the QR runs.
 template <typename T>
 struct ChaseSmem {
-    T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *tau, *vs, *Xb;
+    T *Us, *UTs, *Xs, *Ws, *Ts, *Zs, *Z2s, *tau, *vs, *Xb;
     double *red;
     int ldb1, ldh1;
     __device__ ChaseSmem(unsigned char *base, int b, int h) {
@@ -99,7 +107,8 @@ struct ChaseSmem {
         Ws = Xs + (size_t)ldb1 * b;
         Ts = Ws + (size_t)ldb1 * h;
         Zs = Ts + (size_t)ldh1 * h;
-        tau = Zs + (size_t)ldh1 * h;
+        Z2s = Zs + (size_t)ldh1 * h;
+        tau = Z2s + (size_t)ldh1 * h;
         vs = tau + h;
         size_t off = (size_t)((unsigned char *)(vs + 3 * 128) - base);
         off = (off + 15) & ~(size_t)15;
@@ -118,7 +127,7 @@ __host__ __device__ constexpr int chase_tile_q(int h) {
 template <typename T>
 static size_t band_smem_base(int b, int h) {
     const size_t ldb1 = b + 4, ldh1 = h + 1;
-    size_t e = 3 * ldb1 * h + ldb1 * b + 2 * ldh1 * h + h + 3 * 128;
+    size_t e = 3 * ldb1 * h + ldb1 * b + 3 * ldh1 * h + h + 3 * 128;
     size_t bytes = e * sizeof(T);
     bytes = (bytes + 15) & ~(size_t)15;
     return bytes + 32 * sizeof(double);
@@ -132,6 +141,52 @@ static size_t band_smem_reg(int b, int h) {
 template <typename T>
 size_t band_smem_bytes(int b, int h) {
     return band_smem_base<T>(b, h);
+}
+
+// The qr-row diagonal block X_d (n_r x n_r, mirrored in S.Xs) after U, T
+// and U T are formed: W_d = X_d (U T); S = U^T W_d; Z = T^T S; V_d = -W_d +
+// U Z / 2; X_d += U V_d^T + V_d U^T; the lower triangle written back.
+template <typename T>
+__device__ void chase_diag_update(T *AB, int ldab, int n, int n_r, int nr, int o_qr_r, ChaseSmem<T> &S, int &bad) {
+    const int ldb1 = S.ldb1, ldh1 = S.ldh1;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    constexpr bool kVec = sizeof(T) == 4;
+    cta_mm<T, 4, 4, false, kVec>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, 0, nullptr, 0, nullptr, 0, T(0), S.Ws,
+                                 ldb1);
+    __syncthreads();
+    cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Ws, ldb1, T(0), S.Zs, ldh1);
+    __syncthreads();
+    // Z = T^T S, every entry at once (T upper triangular): Z(a, c) = sum_{q <= a} T(q, a) S(q, c)
+    for (int idx = tid; idx < nr * nr; idx += nt) {
+        const int a = idx % nr, c = idx / nr;
+        T z = 0;
+        for (int q = 0; q <= a; ++q) z += S.Ts[q + (size_t)a * ldh1] * S.Zs[q + (size_t)c * ldh1];
+        S.Z2s[a + (size_t)c * ldh1] = z;
+    }
+    __syncthreads();
+    cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Z2s, ldh1, 0, nullptr, 0, nullptr, 0, T(-1),
+                                 S.Ws, ldb1);
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31, nw = nt >> 5;
+    if (n_r >= 64) {
+        // X_d += [U V_d] [V_d U]^T on the tiles on or below the diagonal
+        cta_mm<T, 8, 8, true, kVec, true>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, nr, S.Ws, ldb1, S.Us, ldb1, T(1),
+                                          S.Xs, ldb1);
+        __syncthreads();
+        // lower triangle, down the columns (band storage: rows of a column contiguous)
+        for (int c = warp; c < n_r; c += nw)
+            for (int r = c + lane; r < n_r; r += 32)
+                bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
+    } else {
+        for (int c = warp; c < n_r; c += nw)
+            for (int r = c + lane; r < n_r; r += 32) {
+                T s = 0;
+                for (int m = 0; m < nr; ++m)
+                    s += S.Us[r + (size_t)m * ldb1] * S.Ws[c + (size_t)m * ldb1] +
+                         S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
+                bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
+            }
+    }
 }
 
 // One chase (i, j) performed by the whole CTA.  RQ, QQ > 0: the n_r x h QR
@@ -174,7 +229,7 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
                     a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
                 }
             BTRACE(1);
-            reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau);
+            reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau, S.Zs, S.Ts, ldh1);
             BTRACE(2);
             // 2. B[qr rows, qr cols] = [R; 0]; U explicit into shared memory
 #pragma unroll
@@ -234,15 +289,18 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         }
         cta_extract_u(n_r, nr, nr, S.Xs, ldb1, S.Us, ldb1);
     }
-    // 3. T and U T (T from G = U^T U by one warp's recurrence when h <= 32)
-    if (nr <= 32) {
-        __syncthreads();
-        cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Us, ldb1, T(0), S.Zs, ldh1);
-        __syncthreads();
-        form_t_from_g(nr, S.Zs, ldh1, S.tau, S.Ts, ldh1);
-    } else {
-        __syncthreads();
-        cta_form_t(n_r, nr, S.Us, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
+    // 3. T (the register QR formed it; else from G = U^T U by one warp's
+    //    recurrence when h <= 32) and U T
+    if constexpr (RQ == 0) {
+        if (nr <= 32) {
+            __syncthreads();
+            cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Us, ldb1, T(0), S.Zs, ldh1);
+            __syncthreads();
+            form_t_from_g(nr, S.Zs, ldh1, S.tau, S.Ts, ldh1);
+        } else {
+            __syncthreads();
+            cta_form_t(n_r, nr, S.Us, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
+        }
     }
     constexpr bool kVec = sizeof(T) == 4;
     cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, 0, nullptr, 0, nullptr, 0, T(0), S.UTs,
@@ -271,53 +329,7 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         __syncthreads();
     }
     BTRACE(6);
-    // W_d = X_d (U T)
-    cta_mm<T, 4, 4, false, kVec>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, 0, nullptr, 0, nullptr, 0, T(0), S.Ws,
-                                 ldb1);
-    __syncthreads();
-    BTRACE(7);
-    // S = U^T W_d
-    cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Ws, ldb1, T(0), S.Zs, ldh1);
-    __syncthreads();
-    BTRACE(8);
-    // Z = T^T S, in place column by column (rows descending)
-    for (int c = tid; c < nr; c += nt) {
-        for (int a = nr - 1; a >= 0; --a) {
-            T s = 0;
-            for (int q = 0; q <= a; ++q) s += S.Ts[q + (size_t)a * ldh1] * S.Zs[q + (size_t)c * ldh1];
-            S.Zs[a + (size_t)c * ldh1] = s;
-        }
-    }
-    __syncthreads();
-    // V_d = -W_d + 1/2 U Z  (into Ws)
-    cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, 0, nullptr, 0, nullptr, 0, T(-1), S.Ws,
-                                 ldb1);
-    __syncthreads();
-    BTRACE(9);
-    // X_d += U V_d^T + V_d U^T, lower half stored: register-tiled products for
-    // wide blocks, one element per thread for narrow ones (more threads busy)
-    if (n_r >= 64) {
-        // one pass over the block: X_d += [U V_d] [V_d U]^T
-        cta_mm<T, 8, 8, true, kVec>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, nr, S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs,
-                                    ldb1);
-        __syncthreads();
-        BTRACE(10);
-        for (int idx = tid; idx < n_r * n_r; idx += nt) {
-            const int r = idx % n_r, c = idx / n_r;
-            if (r < c) continue;
-            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
-        }
-    } else {
-        for (int idx = tid; idx < n_r * n_r; idx += nt) {
-            const int r = idx % n_r, c = idx / n_r;
-            if (r < c) continue;
-            T s = 0;
-            for (int m = 0; m < nr; ++m)
-                s += S.Us[r + (size_t)m * ldb1] * S.Ws[c + (size_t)m * ldb1] +
-                     S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
-            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
-        }
-    }
+    chase_diag_update<T>(AB, ldab, n, n_r, nr, o_qr_r, S, bad);
     __syncthreads();
     BTRACE(4);
     // 5. the other rows of W (above: [0, o_v), below: [o_v + n_r, n_c)):
@@ -472,6 +484,7 @@ __device__ void band_chase_x3(T *AB, int ldab, int n, int b, int h, int i, int j
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr bool kVec = sizeof(T) == 4;
 
+    BTRACE3(0);
     if (rank != 0) {
         // the row block of this rank, loaded while rank 0 factorises
         const bool above = rank == 1;
@@ -489,7 +502,9 @@ __device__ void band_chase_x3(T *AB, int ldab, int n, int b, int h, int i, int j
                     [&](int k, T v) { S.Xs[k % rows + (size_t)(k / rows) * ldb1] = v; });
             }
         }
+        BTRACE3(1);
         cluster_sync();  // A
+        BTRACE3(2);
         int *nr0 = cluster_map(s_nr, 0);
         const int nr = *(volatile int *)nr0;
         if (rows <= 0 || nr <= 0) return;
@@ -503,7 +518,9 @@ __device__ void band_chase_x3(T *AB, int ldab, int n, int b, int h, int i, int j
             dst[at] = src[at];
         }
         __syncthreads();
+        BTRACE3(3);
         chase_rows_update<T>(AB, ldab, n, rows, n_r, nr, o_qr_r, o_up_c + a0, above, S, bad);
+        BTRACE3(4);
         return;
     }
 
@@ -520,7 +537,9 @@ __device__ void band_chase_x3(T *AB, int ldab, int n, int b, int h, int i, int j
                 const int r = lane + 32 * t, c = warp + 4 * q;
                 a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
             }
-        reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau);
+        BTRACE3(1);
+        reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau, S.Zs, S.Ts, ldh1);
+        BTRACE3(2);
 #pragma unroll
         for (int q = 0; q < QQ; ++q)
 #pragma unroll
@@ -552,56 +571,16 @@ __device__ void band_chase_x3(T *AB, int ldab, int n, int b, int h, int i, int j
     }
     if (tid == 0) *s_nr = nr;
     __syncthreads();
-    if (nr > 0) {
-        if (nr <= 32) {
-            cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Us, ldb1, T(0), S.Zs, ldh1);
-            __syncthreads();
-            form_t_from_g(nr, S.Zs, ldh1, S.tau, S.Ts, ldh1);
-        } else {
-            cta_form_t(n_r, nr, S.Us, ldb1, S.tau, S.Ts, ldh1, S.Zs, ldh1);
-        }
+    BTRACE3(3);
+    if (nr > 0)  // T came out of the register QR
         cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(1), S.Us, ldb1, S.Ts, ldh1, 0, nullptr, 0, nullptr, 0, T(0),
                                      S.UTs, ldb1);
-    }
+    BTRACE3(4);
     cluster_sync();  // A: U, U T and nr are ready for ranks 1 and 2
+    BTRACE3(5);
     if (nr == 0) return;
-    // W_d = X_d (U T); S = U^T W_d; Z = T^T S; V_d = -W_d + 1/2 U Z
-    cta_mm<T, 4, 4, false, kVec>(n_r, nr, n_r, T(1), S.Xs, ldb1, S.UTs, ldb1, 0, nullptr, 0, nullptr, 0, T(0), S.Ws,
-                                 ldb1);
-    __syncthreads();
-    cta_gemm<T, true, false>(nr, nr, n_r, T(1), S.Us, ldb1, S.Ws, ldb1, T(0), S.Zs, ldh1);
-    __syncthreads();
-    for (int c = tid; c < nr; c += nt) {
-        for (int a = nr - 1; a >= 0; --a) {
-            T s = 0;
-            for (int q = 0; q <= a; ++q) s += S.Ts[q + (size_t)a * ldh1] * S.Zs[q + (size_t)c * ldh1];
-            S.Zs[a + (size_t)c * ldh1] = s;
-        }
-    }
-    __syncthreads();
-    cta_mm<T, 4, 4, false, kVec>(n_r, nr, nr, T(0.5), S.Us, ldb1, S.Zs, ldh1, 0, nullptr, 0, nullptr, 0, T(-1), S.Ws,
-                                 ldb1);
-    __syncthreads();
-    if (n_r >= 64) {
-        cta_mm<T, 8, 8, true, kVec>(n_r, n_r, nr, T(1), S.Us, ldb1, S.Ws, ldb1, nr, S.Ws, ldb1, S.Us, ldb1, T(1), S.Xs,
-                                    ldb1);
-        __syncthreads();
-        for (int idx = tid; idx < n_r * n_r; idx += nt) {
-            const int r = idx % n_r, c = idx / n_r;
-            if (r < c) continue;
-            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1], bad);
-        }
-    } else {
-        for (int idx = tid; idx < n_r * n_r; idx += nt) {
-            const int r = idx % n_r, c = idx / n_r;
-            if (r < c) continue;
-            T s = 0;
-            for (int m = 0; m < nr; ++m)
-                s += S.Us[r + (size_t)m * ldb1] * S.Ws[c + (size_t)m * ldb1] +
-                     S.Ws[r + (size_t)m * ldb1] * S.Us[c + (size_t)m * ldb1];
-            bst(AB, ldab, n, o_qr_r + r, o_qr_r + c, S.Xs[r + (size_t)c * ldb1] + s, bad);
-        }
-    }
+    chase_diag_update<T>(AB, ldab, n, n_r, nr, o_qr_r, S, bad);
+    BTRACE3(9);
 }
 
 // Capped wait of one thread until sweep s - 1 has completed `need` chases;
@@ -730,9 +709,6 @@ template <typename T>
 static int launch_chase_x3(sev_ctx *hd, int n, T *AB, int ldab, int b, int h, int nsweeps, int *progress, int *ctr,
                            int RQ, int QQ) {
     void (*kern)(int, T *, int, int, int, int, int *, int *, int *) = nullptr;
-    if (RQ == 1 && QQ == 1) kern = band_chase_x3_kernel<T, 1, 1>;
-    if (RQ == 1 && QQ == 2) kern = band_chase_x3_kernel<T, 1, 2>;
-    if (RQ == 1 && QQ == 4) kern = band_chase_x3_kernel<T, 1, 4>;
     if (RQ == 2 && QQ == 1) kern = band_chase_x3_kernel<T, 2, 1>;
     if (RQ == 2 && QQ == 2) kern = band_chase_x3_kernel<T, 2, 2>;
     if (RQ == 2 && QQ == 4) kern = band_chase_x3_kernel<T, 2, 4>;

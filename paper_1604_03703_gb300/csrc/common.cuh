@@ -274,8 +274,8 @@ __device__ __forceinline__ F2 two_prod(float a, float b) {
     const float p = a * b;
     return {p, fmaf(a, b, -p)};
 }
-__device__ __forceinline__ void house_scalars_f2(float alpha, F2 ssq, float *tau, float *beta, float *inv) {
-    const F2 s = f2_add(ssq, two_prod(alpha, alpha));
+// The same from s = alpha^2 + ssq given directly (pair-float).
+__device__ __forceinline__ void house_scalars_f2s(float alpha, F2 s, float *tau, float *beta, float *inv) {
     if (!(s.hi > 0.f)) {
         *tau = *beta = *inv = 0.f;
         return;
@@ -298,6 +298,9 @@ __device__ __forceinline__ void house_scalars_f2(float alpha, F2 ssq, float *tau
     const float e = fmaf(-d.hi, r0, 1.0f) - d.lo * r0;  // 1 - d r0
     const float iv = fmaf(r0, e, r0);
     *inv = alpha < 0.f ? -iv : iv;  // alpha - beta = sgn(alpha) d
+}
+__device__ __forceinline__ void house_scalars_f2(float alpha, F2 ssq, float *tau, float *beta, float *inv) {
+    house_scalars_f2s(alpha, f2_add(ssq, two_prod(alpha, alpha)), tau, beta, inv);
 }
 
 // Reflector of the column segment x[0..m-1] (shared memory, stride 1),
@@ -636,14 +639,29 @@ __device__ void cta_gemm(int M, int N, int K, T alpha, const T *A, int lda, cons
 // multiples of 4 and the bases 16-byte aligned, so full tiles use float4
 // loads; ragged tiles fall back to clamped scalar reads (never outside the
 // M x K / K x N operands).  Each output sums its k terms in order (A1 B1
-// first); no barrier inside.
-template <typename T, int TM, int TN, bool BT, bool VEC>
+// first); no barrier inside.  LOWER (M = N, TM = TN): only the tiles on or
+// below the diagonal are computed, numbered consecutively so that the busy
+// threads fill whole warps (the diagonal tiles are computed in full).
+template <typename T, int TM, int TN, bool BT, bool VEC, bool LOWER = false>
 __device__ void cta_mm(int M, int N, int K1, T alpha, const T *A1, int lda1, const T *B1, int ldb1, int K2,
                        const T *A2, int lda2, const T *B2, int ldb2, T beta, T *C, int ldc) {
     static_assert(!VEC || (sizeof(T) == 4 && TM % 4 == 0 && (!BT || TN % 4 == 0)), "vector loads need float tiles");
+    static_assert(!LOWER || TM == TN, "lower-triangle tiles need square tiles");
     const int Mb = (M + TM - 1) / TM, Nb = (N + TN - 1) / TN;
-    for (int blk = threadIdx.x; blk < Mb * Nb; blk += blockDim.x) {
-        const int m0 = (blk % Mb) * TM, n0 = (blk / Mb) * TN;
+    const int ntiles = LOWER ? Mb * (Mb + 1) / 2 : Mb * Nb;
+    for (int blk = threadIdx.x; blk < ntiles; blk += blockDim.x) {
+        int m0, n0;
+        if constexpr (LOWER) {
+            // tile t of the lower triangle, row by row: I (I + 1) / 2 <= t
+            int I = (int)((sqrtf(8.f * (float)blk + 1.f) - 1.f) * 0.5f);
+            while ((I + 1) * (I + 2) / 2 <= blk) ++I;
+            while (I * (I + 1) / 2 > blk) --I;
+            m0 = I * TM;
+            n0 = (blk - I * (I + 1) / 2) * TN;
+        } else {
+            m0 = (blk % Mb) * TM;
+            n0 = (blk / Mb) * TN;
+        }
         const bool full = m0 + TM <= M && n0 + TN <= N;
         T acc[TM][TN];
 #pragma unroll

@@ -77,7 +77,7 @@ struct RowBlocks {
 // reduced together so their shuffle chains overlap.
 template <typename T, int R, int Q>
 __device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const bool (&act)[R], T tau,
-                                          const T (&cm)[Q]) {
+                                          const T (&cm)[Q], T (&dq)[Q]) {
     T d[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) d[q] = T(0);
@@ -93,7 +93,10 @@ __device__ __forceinline__ void reg_apply(T (&a)[Q][R], const T (&vr)[R], const 
         for (int q = 0; q < Q; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
     T sc[Q];
 #pragma unroll
-    for (int q = 0; q < Q; ++q) sc[q] = tau * d[q] * cm[q];
+    for (int q = 0; q < Q; ++q) {
+        dq[q] = d[q];
+        sc[q] = tau * d[q] * cm[q];
+    }
 #pragma unroll
     for (int t = 0; t < R; ++t)
         if (act[t]) {
@@ -166,7 +169,7 @@ __device__ __forceinline__ void warp_sums_x(float (&d)[Q]) {
 // warp_sums_x.
 template <int R, int Q>
 __device__ __forceinline__ void reg_apply_f32x2(float (&a)[Q][R], const float (&vr)[R], const bool (&act)[R],
-                                                float tau, const float (&cm)[Q]) {
+                                                float tau, const float (&cm)[Q], float (&dq)[Q]) {
     float2 dd[Q / 2];
 #pragma unroll
     for (int p = 0; p < Q / 2; ++p) dd[p] = make_float2(0.f, 0.f);
@@ -184,6 +187,8 @@ __device__ __forceinline__ void reg_apply_f32x2(float (&a)[Q][R], const float (&
         d[2 * p + 1] = dd[p].y;
     }
     warp_sums_x<Q>(d);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) dq[q] = d[q];
     float2 ms[Q / 2];
 #pragma unroll
     for (int p = 0; p < Q / 2; ++p) ms[p] = make_float2(-tau * d[2 * p] * cm[2 * p], -tau * d[2 * p + 1] * cm[2 * p + 1]);
@@ -218,6 +223,26 @@ __device__ __forceinline__ void reg_col_put(T (&a)[Q][R], int q, const T (&x)[R]
 #pragma unroll
             for (int t = 0; t < R; ++t) a[i][t] = x[t];
         }
+}
+
+// x <- [rows < k unchanged; beta at row k; v below] and vout <- v (0 above
+// row k, 1 at k), from the scalars of the reflector.
+template <typename T, int R>
+__device__ __forceinline__ void reg_house_store(T (&x)[R], int k, T tau, T beta, T inv, T *vout) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+        const int row = lane + 32 * t;
+        if (row == k) {
+            x[t] = beta;
+            vout[row] = T(1);
+        } else if (row > k) {
+            if (tau != T(0)) x[t] = x[t] * inv;
+            vout[row] = x[t];
+        } else {
+            vout[row] = T(0);
+        }
+    }
 }
 
 // Reflector of rows k..m-1 of the column x (one warp; lane rows lane + 32 t;
@@ -294,26 +319,19 @@ __device__ __forceinline__ T reg_house(T (&x)[R], int k, T *vout) {
         beta = (T)bd;
         inv = (T)id;
     }
-#pragma unroll
-    for (int t = 0; t < R; ++t) {
-        const int row = lane + 32 * t;
-        if (row == k) {
-            x[t] = beta;
-            vout[row] = T(1);
-        } else if (row > k) {
-            if (tau != T(0)) x[t] = x[t] * inv;
-            vout[row] = x[t];
-        } else {
-            vout[row] = T(0);
-        }
-    }
+    reg_house_store<T, R>(x, k, tau, beta, inv, vout);
     return tau;
 }
 
 // Householder QR of the m x nc block held in `a` (m <= 32R, nc <= NW Q;
 // rows >= m and columns >= nc zero), r = min(nc, m - 1) reflectors.  On
 // return column c holds R above and on the diagonal and v_c below it (unit
-// diagonal implicit); taus[c] = tau_c.  vs: 3 x 32R shared scratch.
+// diagonal implicit); taus[c] = tau_c.  vs: 3 x 32R shared scratch.  With
+// Gm and Tm (shared, leading dimension ldg >= r) the compact-WY factor T of
+// the r reflectors is formed on the way (into Tm; Gm receives G = V^T V
+// above its diagonal): every dot product of a reflector with a finished
+// column is an entry of G that the trailing update computes anyway, and
+// column k - 2 of T is formed in step k by an otherwise waiting warp.
 //
 // Step k applies reflector k.  The warp owning column k + 1 first brings
 // that column up to date and forms reflector k + 1 from it (lookahead); it
@@ -336,13 +354,23 @@ __device__ __forceinline__ void reg_sync() {
 }
 
 // The reflector in buffer slot k % 3, restricted to the row blocks it can
-// touch, applied to this warp's columns c with lo < c < nc.
+// touch, applied to this warp's columns c with lo < c < nc; with Gm, the
+// dot products with the finished columns are kept as entries of G.
 template <typename T, int R, int Q, int NW>
 __device__ __forceinline__ void reg_apply_step(T (&a)[Q][R], const RowBlocks<R> &blk, const T *vs, const T *taus,
-                                               int k, int lo, int nc) {
+                                               int k, int lo, int nc, T *Gm, int ldg) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const T tk = taus[k];
-    if (tk == T(0)) return;
+    if (tk == T(0)) {
+        if (Gm && lane == 0) {  // T's column k is zero then; no stale value reaches it
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const int c = warp + NW * q;
+                if (c < k) Gm[c + (size_t)k * ldg] = T(0);
+            }
+        }
+        return;
+    }
     const T *v = vs + (k % 3) * (32 * R);
     bool act[R];
     T vr[R];
@@ -357,14 +385,46 @@ __device__ __forceinline__ void reg_apply_step(T (&a)[Q][R], const RowBlocks<R> 
         const int c = warp + NW * q;
         cm[q] = (c > lo && c < nc) ? T(1) : T(0);
     }
+    T dq[Q];
     if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
-        reg_apply_f32x2<R, Q>(a, vr, act, tk, cm);
+        reg_apply_f32x2<R, Q>(a, vr, act, tk, cm, dq);
     else
-        reg_apply<T, R, Q>(a, vr, act, tk, cm);
+        reg_apply<T, R, Q>(a, vr, act, tk, cm, dq);
+    // G(c, k) = v_c^T v_k for this warp's finished columns c < k: the dot
+    // of reflector k with column c (rows >= k hold v_c there)
+    if (Gm && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int c = warp + NW * q;
+            if (c < k) Gm[c + (size_t)k * ldg] = dq[q];
+        }
+    }
+}
+
+// Column k of the compact-WY factor T (forward, column-wise: Q = I - V T V^T,
+// T upper triangular, r x r) by one warp: T(k, k) = tau_k, for a < k
+// T(a, k) = -tau_k sum_{q = a}^{k-1} T(a, q) G(q, k) with G = V^T V, and
+// zeros below the diagonal.
+template <typename T>
+__device__ __forceinline__ void reg_t_column(int k, int r, const T *taus, const T *Gm, T *Tm, int ldg) {
+    const int lane = threadIdx.x & 31;
+    const T tk = taus[k];
+    for (int a = k + 1 + lane; a < r; a += 32) Tm[a + (size_t)k * ldg] = T(0);
+    for (int a = lane; a <= k; a += 32) {
+        T s0 = 0, s1 = 0;
+        int q = a;
+        for (; q + 1 < k; q += 2) {
+            s0 += Tm[a + (size_t)q * ldg] * Gm[q + (size_t)k * ldg];
+            s1 += Tm[a + (size_t)(q + 1) * ldg] * Gm[q + 1 + (size_t)k * ldg];
+        }
+        if (q < k) s0 += Tm[a + (size_t)q * ldg] * Gm[q + (size_t)k * ldg];
+        Tm[a + (size_t)k * ldg] = a == k ? tk : -tk * (s0 + s1);
+    }
 }
 
 template <typename T, int R, int Q, int NW, int BAR = 0>
-__device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
+__device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus, T *Gm = nullptr,
+                      T *Tm = nullptr, int ldg = 0) {
     static_assert(NW >= 2, "reg_qr: the owner of a column and of the next one must differ");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int r = nc < m - 1 ? nc : m - 1;
@@ -401,7 +461,8 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
             reg_col_get<T, R, Q>(a, q1, x[0]);
             if (tk != T(0)) {
                 const T one[1] = {T(1)};
-                reg_apply<T, R, 1>(x, vr, act, tk, one);
+                T d1[1];
+                reg_apply<T, R, 1>(x, vr, act, tk, one, d1);
             }
             RTRACE(k, 1);
             if (k1 < r) {
@@ -416,12 +477,27 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus) {
             // the update code is emitted once
             const bool deferred = k >= 1 && k < nc && (k % NW) == warp;
             const int kend = step ? k : k - 1;
-            for (int kk = deferred ? k - 1 : k; kk <= kend; ++kk) reg_apply_step<T, R, Q, NW>(a, blk, vs, taus, kk, k, nc);
+            for (int kk = deferred ? k - 1 : k; kk <= kend; ++kk)
+                reg_apply_step<T, R, Q, NW>(a, blk, vs, taus, kk, k, nc, Gm, ldg);
+            // T's column k - 2 (G(., k - 2) is complete since the last
+            // barrier) by a warp that neither owns column k + 1 nor is
+            // catching up (warp k mod NW): warp (k + 2) mod NW
+            if (Tm && NW >= 3 && step && k >= 2 && warp == (k + 2) % NW) reg_t_column<T>(k - 2, r, taus, Gm, Tm, ldg);
         }
         if (step) {
             if (k1 < nc && (k1 % NW) == warp) RTRACE(k, 3);
             reg_sync<NW, BAR>();
         }
+    }
+    if (Tm) {
+        // the last columns of T (all of them with two warps), in order
+        reg_sync<NW, BAR>();
+        if (warp == 0)
+            for (int k = (NW >= 3 ? (r - 2 > 0 ? r - 2 : 0) : 0); k < r; ++k) {
+                reg_t_column<T>(k, r, taus, Gm, Tm, ldg);
+                __syncwarp();
+            }
+        reg_sync<NW, BAR>();
     }
     return r;
 }
@@ -443,10 +519,11 @@ __device__ void reg_apply_all(T (&m)[Q][R], const T *Vs, int ldv, const T *taus,
             act[t] = blk.active(t, k);
             vr[t] = act[t] ? Vs[(size_t)k * ldv + lane + 32 * t] : T(0);
         }
+        T dq[Q];
         if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
-            reg_apply_f32x2<R, Q>(m, vr, act, tk, cm);
+            reg_apply_f32x2<R, Q>(m, vr, act, tk, cm, dq);
         else
-            reg_apply<T, R, Q>(m, vr, act, tk, cm);
+            reg_apply<T, R, Q>(m, vr, act, tk, cm, dq);
     }
 }
 
