@@ -51,12 +51,12 @@ __host__ __device__ __forceinline__ int rleaf_row0(int N, int L, int l) { return
 // Leaf QR: CTA l factorises its rows of the N x b panel P (ldp).  Writes the
 // explicit unit lower trapezoidal V into Y (rows of the leaf, ldy), tau,
 // the number of reflectors and R (b x b, upper) into Rbuf[l].
-template <typename T, int R, int Q>
-__global__ void __launch_bounds__(kRegThreads, 1)
+template <typename T, int R, int Q, int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
     rtsqr_leaf_qr_kernel(const T *__restrict__ P, int ldp, int N, int b, int L, T *__restrict__ Y, int ldy,
                          T *__restrict__ tau, int *__restrict__ nref, T *__restrict__ Rbuf) {
     __shared__ __align__(16) T vs[3 * 32 * R];
-    __shared__ T taus[kRegWarps * Q];
+    __shared__ T taus[NW * Q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int l = blockIdx.x;
     const int row0 = rleaf_row0(N, L, l);
@@ -66,16 +66,16 @@ __global__ void __launch_bounds__(kRegThreads, 1)
     for (int q = 0; q < Q; ++q)
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            const int c = warp + kRegWarps * q, r = lane + 32 * t;
+            const int c = warp + NW * q, r = lane + 32 * t;
             a[q][t] = (c < b && r < rows) ? P[(size_t)(row0 + r) + (size_t)c * ldp] : T(0);
         }
-    const int nr = reg_qr<T, R, Q, kRegWarps>(a, rows, b, 0, vs, taus);
+    const int nr = reg_qr<T, R, Q, NW>(a, rows, b, 0, vs, taus);
     T *Rl = Rbuf + (size_t)l * b * b;
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            const int c = warp + kRegWarps * q, r = lane + 32 * t;
+            const int c = warp + NW * q, r = lane + 32 * t;
             if (c >= b) continue;
             if (r < rows) {
                 T v = T(0);
@@ -90,12 +90,12 @@ __global__ void __launch_bounds__(kRegThreads, 1)
 
 // Node QR: CTA p of a level stacks the R's of its two children (one child:
 // pass-through) and factorises the 2b x b stack of upper triangles.
-template <typename T, int R, int Q>
-__global__ void __launch_bounds__(kRegThreads, 1)
+template <typename T, int R, int Q, int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
     rtsqr_node_qr_kernel(int b, int cnt_child, int off_child, int off_node, T *__restrict__ Rbuf,
                          T *__restrict__ Ylev, size_t ystride, T *__restrict__ tau, int *__restrict__ nref) {
     __shared__ __align__(16) T vs[3 * 32 * R];
-    __shared__ T taus[kRegWarps * Q];
+    __shared__ T taus[NW * Q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int p = blockIdx.x;
     const int c0 = 2 * p, nc = min(2, cnt_child - c0);
@@ -113,18 +113,18 @@ __global__ void __launch_bounds__(kRegThreads, 1)
     for (int q = 0; q < Q; ++q)
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            const int c = warp + kRegWarps * q, r = lane + 32 * t;
+            const int c = warp + NW * q, r = lane + 32 * t;
             const int i = r % b;
             a[q][t] = (c < b && r < rows && i <= c) ? Rbuf[(size_t)(off_child + c0 + r / b) * b * b + i + (size_t)c * b]
                                                      : T(0);
         }
-    const int nr = reg_qr<T, R, Q, kRegWarps>(a, rows, b, b % 32 == 0 ? b : 0, vs, taus);
+    const int nr = reg_qr<T, R, Q, NW>(a, rows, b, b % 32 == 0 ? b : 0, vs, taus);
     T *Y = Ylev + (size_t)p * ystride;
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
         for (int t = 0; t < R; ++t) {
-            const int c = warp + kRegWarps * q, r = lane + 32 * t;
+            const int c = warp + NW * q, r = lane + 32 * t;
             if (c >= b) continue;
             if (r < rows) {
                 T v = T(0);
@@ -416,8 +416,14 @@ int reg_panel_supported(int b) {
     return sizeof(T) == 4 ? b <= 128 : b <= 64;
 }
 
-template <typename T, int R, int Q, int RR>
+// Q, RR: columns per warp of the 16-warp kernels (applies, reconstruction);
+// QW, NWQ: columns per warp and warps of the leaf and node QRs.
+#ifndef SEV_QR128_QW
+#define SEV_QR128_QW 16  // b = 128 FP32: 8 warps x 16 columns for the tree QR
+#endif
+template <typename T, int R, int Q, int RR, int QW = Q, int NWQ = kRegWarps>
 static int reg_panel_run(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, const RegPanelBufs<T> &B) {
+    static_assert(NWQ * QW == kRegWarps * Q, "the QR kernels hold the same columns");
     // leaves: as many as 256-row blocks need (each >= b rows when there are
     // two or more), or rows of about SEV_LEAF_ROWS (tests: deep trees)
     int L = (N + 32 * R - 1) / (32 * R);
@@ -430,11 +436,11 @@ static int reg_panel_run(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, c
     if (L < 1) L = 1;
     if (L == 1) {
         // one leaf: its Householder QR already is (U, T); T by the forward recurrence
-        SEV_LAUNCH(h, K_TSQR_LEAF, (rtsqr_leaf_qr_kernel<T, R, Q>), 1, kRegThreads, 0, P, lda, N, b, 1, U, N, B.tau,
+        SEV_LAUNCH(h, K_TSQR_LEAF, (rtsqr_leaf_qr_kernel<T, R, QW, NWQ>), 1, NWQ * 32, 0, P, lda, N, b, 1, U, N, B.tau,
                    B.nref, B.Rbuf);
         return panel_finish_single_leaf<T>(h, N, b, U, B.tau, B.nref, B.Rbuf, Tm, P, lda);
     }
-    SEV_LAUNCH(h, K_TSQR_LEAF, (rtsqr_leaf_qr_kernel<T, R, Q>), L, kRegThreads, 0, P, lda, N, b, L, B.Yleaf, N, B.tau,
+    SEV_LAUNCH(h, K_TSQR_LEAF, (rtsqr_leaf_qr_kernel<T, R, QW, NWQ>), L, NWQ * 32, 0, P, lda, N, b, L, B.Yleaf, N, B.tau,
                B.nref, B.Rbuf);
     int cnt[32], off[32], nlev = 0;
     for (int c = L, o = 0;; c = (c + 1) / 2) {
@@ -447,7 +453,7 @@ static int reg_panel_run(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, c
     const size_t ystride = (size_t)2 * b * b;
     for (int lev = 1; lev < nlev; ++lev) {
         T *Ylev = B.Ynode + (size_t)(off[lev] - L) * ystride;
-        SEV_LAUNCH(h, K_TSQR_TREE, (rtsqr_node_qr_kernel<T, R, Q>), cnt[lev], kRegThreads, 0, b, cnt[lev - 1],
+        SEV_LAUNCH(h, K_TSQR_TREE, (rtsqr_node_qr_kernel<T, R, QW, NWQ>), cnt[lev], NWQ * 32, 0, b, cnt[lev - 1],
                    off[lev - 1], off[lev], B.Rbuf, Ylev, ystride, B.tau, B.nref);
     }
     // the way down: the upper levels have few nodes, so 32-column slices
@@ -480,7 +486,7 @@ template <typename T>
 int reg_panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, const RegPanelBufs<T> &B) {
     if (b <= 32) return reg_panel_run<T, 8, 2, 1>(h, N, b, P, lda, U, Tm, B);
     if (b <= 64) return reg_panel_run<T, 8, 4, 2>(h, N, b, P, lda, U, Tm, B);
-    if constexpr (sizeof(T) == 4) return reg_panel_run<T, 8, 8, 4>(h, N, b, P, lda, U, Tm, B);
+    if constexpr (sizeof(T) == 4) return reg_panel_run<T, 8, 8, 4, SEV_QR128_QW, 128 / SEV_QR128_QW>(h, N, b, P, lda, U, Tm, B);
     return SEV_ERR_UNSUPPORTED;
 }
 

@@ -122,7 +122,7 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return d;
 }
 
-// Warp sums of Q per-lane values (Q = 2, 4, 8) by a transposing butterfly:
+// Warp sums of Q per-lane values (Q = 2, 4, 8, 16) by a transposing butterfly:
 // at each of the first log2 Q levels a lane keeps half of its remaining
 // values and sends the other half to its partner, so the shuffles total
 // Q - 1 + (5 - log2 Q) + Q (the last Q broadcast the sums) instead of 5 Q.
@@ -131,7 +131,21 @@ template <int Q>
 __device__ __forceinline__ void warp_sums_x(float (&d)[Q]) {
     const int lane = threadIdx.x & 31;
     float c;
-    if constexpr (Q == 8) {
+    if constexpr (Q == 16) {
+        const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4, u2 = lane & 2;
+        float a8[8], a4[4], b2[2];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a8[j] = (u16 ? d[j + 8] : d[j]) + __shfl_xor_sync(0xffffffffu, u16 ? d[j] : d[j + 8], 16);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a4[j] = (u8 ? a8[j + 4] : a8[j]) + __shfl_xor_sync(0xffffffffu, u8 ? a8[j] : a8[j + 4], 8);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) b2[j] = (u4 ? a4[j + 2] : a4[j]) + __shfl_xor_sync(0xffffffffu, u4 ? a4[j] : a4[j + 2], 4);
+        c = (u2 ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, u2 ? b2[0] : b2[1], 2);
+        c += __shfl_xor_sync(0xffffffffu, c, 1);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            d[q] = __shfl_sync(0xffffffffu, c, ((q >> 3) & 1) * 16 + ((q >> 2) & 1) * 8 + ((q >> 1) & 1) * 4 + (q & 1) * 2);
+    } else if constexpr (Q == 8) {
         const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
         float a4[4], b2[2];
 #pragma unroll
@@ -154,7 +168,7 @@ __device__ __forceinline__ void warp_sums_x(float (&d)[Q]) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) d[q] = __shfl_sync(0xffffffffu, c, ((q >> 1) & 1) * 16 + (q & 1) * 8);
     } else {
-        static_assert(Q == 2, "warp_sums_x: Q = 2, 4 or 8");
+        static_assert(Q == 2, "warp_sums_x: Q = 2, 4, 8 or 16");
         const bool u16 = lane & 16;
         c = (u16 ? d[1] : d[0]) + __shfl_xor_sync(0xffffffffu, u16 ? d[0] : d[1], 16);
 #pragma unroll
@@ -164,7 +178,7 @@ __device__ __forceinline__ void warp_sums_x(float (&d)[Q]) {
     }
 }
 
-// reg_apply for FP32 tiles of 2, 4 or 8 columns per warp: the dot products
+// reg_apply for FP32 tiles of 2, 4, 8 or 16 columns per warp: the dot products
 // and the updates two columns per instruction (ffma2), the column sums by
 // warp_sums_x.
 template <int R, int Q>
@@ -386,7 +400,7 @@ __device__ __forceinline__ void reg_apply_step(T (&a)[Q][R], const RowBlocks<R> 
         cm[q] = (c > lo && c < nc) ? T(1) : T(0);
     }
     T dq[Q];
-    if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
+    if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8 || Q == 16))
         reg_apply_f32x2<R, Q>(a, vr, act, tk, cm, dq);
     else
         reg_apply<T, R, Q>(a, vr, act, tk, cm, dq);
@@ -520,7 +534,7 @@ __device__ void reg_apply_all(T (&m)[Q][R], const T *Vs, int ldv, const T *taus,
             vr[t] = act[t] ? Vs[(size_t)k * ldv + lane + 32 * t] : T(0);
         }
         T dq[Q];
-        if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8))
+        if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8 || Q == 16))
             reg_apply_f32x2<R, Q>(m, vr, act, tk, cm, dq);
         else
             reg_apply<T, R, Q>(m, vr, act, tk, cm, dq);
