@@ -484,8 +484,13 @@ static int reg_panel_run(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, c
 
 template <typename T>
 int reg_panel_factor(sev_ctx *h, int N, int b, T *P, int lda, T *U, T *Tm, const RegPanelBufs<T> &B) {
-    if (b <= 32) return reg_panel_run<T, 8, 2, 1>(h, N, b, P, lda, U, Tm, B);
-    if (b <= 64) return reg_panel_run<T, 8, 4, 2>(h, N, b, P, lda, U, Tm, B);
+    if constexpr (sizeof(T) == 4) {  // FP32: the QRs on 8 warps (twice the columns each)
+        if (b <= 32) return reg_panel_run<T, 8, 2, 1, 4, 8>(h, N, b, P, lda, U, Tm, B);
+        if (b <= 64) return reg_panel_run<T, 8, 4, 2, 8, 8>(h, N, b, P, lda, U, Tm, B);
+    } else {
+        if (b <= 32) return reg_panel_run<T, 8, 2, 1>(h, N, b, P, lda, U, Tm, B);
+        if (b <= 64) return reg_panel_run<T, 8, 4, 2>(h, N, b, P, lda, U, Tm, B);
+    }
     if constexpr (sizeof(T) == 4) return reg_panel_run<T, 8, 8, 4, SEV_QR128_QW, 128 / SEV_QR128_QW>(h, N, b, P, lda, U, Tm, B);
     return SEV_ERR_UNSUPPORTED;
 }
