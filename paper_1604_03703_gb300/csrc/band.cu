@@ -217,35 +217,10 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
         const int warp = tid >> 5, lane = tid & 31;
         nr = n_r - 1 < h ? n_r - 1 : h;
         if (nr < 0) nr = 0;
-        if (warp < 4) {
-            // 1. warps 0-3: QR of the n_r x h block in registers (lane rows,
-            //    warp-cyclic columns), one warp per scheduler
-            T a[QQ][RQ];
-#pragma unroll
-            for (int q = 0; q < QQ; ++q)
-#pragma unroll
-                for (int t = 0; t < RQ; ++t) {
-                    const int r = lane + 32 * t, c = warp + 4 * q;
-                    a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
-                }
-            BTRACE(1);
-            reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau, S.Zs, S.Ts, ldh1);
-            BTRACE(2);
-            // 2. B[qr rows, qr cols] = [R; 0]; U explicit into shared memory
-#pragma unroll
-            for (int q = 0; q < QQ; ++q)
-#pragma unroll
-                for (int t = 0; t < RQ; ++t) {
-                    const int r = lane + 32 * t, c = warp + 4 * q;
-                    if (r < n_r && c < h) {
-                        bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, r <= c ? a[q][t] : T(0), bad);
-                        if (c < nr) S.Us[r + (size_t)c * ldb1] = r < c ? T(0) : (r == c ? T(1) : a[q][t]);
-                    }
-                }
-        } else if (nr > 0) {
-            // warps 4-7 meanwhile: the diagonal block (stored lower triangle,
-            // read down its columns, then mirrored) and the rows above the qr
-            // rows (element (row, col) stored as (col, row): read along col)
+        // warps 4-7 meanwhile: the diagonal block (stored lower triangle,
+        // read down its columns, then mirrored) and the rows above the qr
+        // rows (element (row, col) stored as (col, row): read along col)
+        auto load_diag_and_above = [&]() {
             const int t4 = tid - 128;
             batched_copy<T>(
                 n_r * n_r, t4, 128,
@@ -264,6 +239,58 @@ __device__ void band_chase(T *AB, int ldab, int n, int b, int h, int i, int j, C
             for (int idx = t4; idx < n_r * n_r; idx += 128) {
                 const int r = idx % n_r, c = idx / n_r;
                 if (r < c) S.Xs[r + (size_t)c * ldb1] = S.Xs[c + (size_t)r * ldb1];
+            }
+        };
+        if constexpr (RQ == 1 && QQ <= 2) {
+            if (warp == 0) {
+                // 1. (n_r <= 32, h <= 8) warp 0 alone: QR of the n_r x h block,
+                //    lane rows, all h columns in its registers, T formed on the
+                //    way (for h = 16 the 4-warp QR below is faster)
+                constexpr int QW = 4 * QQ;
+                T a[QW];
+#pragma unroll
+                for (int c = 0; c < QW; ++c)
+                    a[c] = (lane < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + lane, o_qr_c + c, bad) : T(0);
+                BTRACE(1);
+                warp_qr<T, QW>(a, n_r, h, S.vs, S.tau, S.Ts, ldh1);
+                BTRACE(2);
+#pragma unroll
+                for (int c = 0; c < QW; ++c)
+                    if (lane < n_r && c < h) {
+                        bst(AB, ldab, n, o_qr_r + lane, o_qr_c + c, lane <= c ? a[c] : T(0), bad);
+                        if (c < nr) S.Us[lane + (size_t)c * ldb1] = lane < c ? T(0) : (lane == c ? T(1) : a[c]);
+                    }
+            } else if (warp >= 4 && nr > 0) {
+                load_diag_and_above();
+            }
+        } else {
+            if (warp < 4) {
+                // 1. warps 0-3: QR of the n_r x h block in registers (lane rows,
+                //    warp-cyclic columns), one warp per scheduler
+                T a[QQ][RQ];
+#pragma unroll
+                for (int q = 0; q < QQ; ++q)
+#pragma unroll
+                    for (int t = 0; t < RQ; ++t) {
+                        const int r = lane + 32 * t, c = warp + 4 * q;
+                        a[q][t] = (r < n_r && c < h) ? bld(AB, ldab, n, o_qr_r + r, o_qr_c + c, bad) : T(0);
+                    }
+                BTRACE(1);
+                reg_qr<T, RQ, QQ, 4, 1>(a, n_r, h, 0, S.vs, S.tau, S.Zs, S.Ts, ldh1);
+                BTRACE(2);
+                // 2. B[qr rows, qr cols] = [R; 0]; U explicit into shared memory
+#pragma unroll
+                for (int q = 0; q < QQ; ++q)
+#pragma unroll
+                    for (int t = 0; t < RQ; ++t) {
+                        const int r = lane + 32 * t, c = warp + 4 * q;
+                        if (r < n_r && c < h) {
+                            bst(AB, ldab, n, o_qr_r + r, o_qr_c + c, r <= c ? a[q][t] : T(0), bad);
+                            if (c < nr) S.Us[r + (size_t)c * ldb1] = r < c ? T(0) : (r == c ? T(1) : a[q][t]);
+                        }
+                    }
+            } else if (nr > 0) {
+                load_diag_and_above();
             }
         }
         __syncthreads();

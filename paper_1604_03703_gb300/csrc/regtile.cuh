@@ -516,6 +516,63 @@ __device__ int reg_qr(T (&a)[Q][R], int m, int nc, int bstack, T *vs, T *taus, T
     return r;
 }
 
+// Householder QR of an m x nc block (m <= 32, nc <= Q) held by ONE warp:
+// lane l keeps row l of every column (a[q] = M(l, q)).  No barrier: each
+// step forms reflector k from column k (reg_house; v through the 32-entry
+// scratch vs) and applies it to the later columns, the dot products of all
+// columns summed together (transposing butterfly); the sums for the
+// finished columns are G(q, k) = v_q^T v_k, from which lane a forms row a
+// of the compact-WY factor T (forward, column-wise) in registers:
+// T(a, k) = -tau_k sum_{q = a}^{k-1} T(a, q) G(q, k), T(k, k) = tau_k.  On
+// return column c holds R on and above the diagonal and v_c below; taus[c]
+// and T (r x r, leading dimension ldt, zeros below the diagonal) are in
+// shared memory; returns r = min(nc, m - 1).
+template <typename T, int Q>
+__device__ int warp_qr(T (&a)[Q], int m, int nc, T *vs, T *taus, T *Tm, int ldt) {
+    const int lane = threadIdx.x & 31;
+    int r = nc < m - 1 ? nc : m - 1;
+    if (r < 0) r = 0;
+    T trow[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) trow[q] = T(0);
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+        if (k < r) {
+            T x[1] = {a[k]};
+            const T tk = reg_house<T, 1>(x, k, vs);
+            a[k] = x[0];
+            __syncwarp();
+            const T v = vs[lane];
+            __syncwarp();
+            T d[Q];
+#pragma unroll
+            for (int q = 0; q < Q; ++q) d[q] = q == k ? T(0) : v * a[q];
+            if constexpr (sizeof(T) == 4 && (Q == 2 || Q == 4 || Q == 8 || Q == 16)) {
+                warp_sums_x<Q>(d);
+            } else {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+            }
+#pragma unroll
+            for (int q = k + 1; q < Q; ++q) a[q] = fmat(-tk * d[q], v, a[q]);
+            T sacc = T(0);
+#pragma unroll
+            for (int q = 0; q < k; ++q) sacc = fmat(trow[q], d[q], sacc);
+            trow[k] = lane < k ? -tk * sacc : (lane == k ? tk : T(0));
+            if (lane == 0) taus[k] = tk;
+        }
+    }
+    if (lane < r) {
+#pragma unroll
+        for (int q = 0; q < Q; ++q)
+            if (q < r) Tm[lane + (size_t)q * ldt] = trow[q];
+    }
+    __syncwarp();
+    return r;
+}
+
 // M <- H_0 H_1 ... H_{nr-1} M: reflectors explicit in Vs (column k at
 // Vs[k * ldv], rows 0 .. 32R), scalars in taus; columns of M with cm[q] = 1.
 template <typename T, int R, int Q>
