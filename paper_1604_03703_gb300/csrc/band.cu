@@ -31,6 +31,10 @@ static __device__ long long *sev_btrace = nullptr;
 extern "C" int sev_trace_set_band(void *p) {
     return cudaMemcpyToSymbol(sev_btrace, &p, sizeof(p)) == cudaSuccess ? 0 : 1;
 }
+// the register QR's step clocks of CTA 0 (this file's copy of the trace pointer)
+extern "C" int sev_trace_set_reg_band(void *p) {
+    return cudaMemcpyToSymbol(sev_rtrace, &p, sizeof(p)) == cudaSuccess ? 0 : 1;
+}
 #define BTRACE(k)                                                              \
     do {                                                                       \
         if (threadIdx.x == 0 && sev_btrace && i == 40 && j == 20) sev_btrace[k] = clock64(); \

@@ -160,7 +160,10 @@ __global__ void __launch_bounds__((G + 2) * 32, 1)
                         if (warp == 0 && lane == 0 && gi == 1 && j == 40) sev_trace_phase_on = blockIdx.x + 1;
                         __syncwarp();
 #endif
-                        tri_chase<T, B>(n, o, j, j < Ji, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
+                        if (j > 1 && j < Ji && o + 3 * B <= n)
+                            tri_chase<T, B, true>(n, o, j, true, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
+                        else
+                            tri_chase<T, B>(n, o, j, j < Ji, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
 #ifdef SEV_TRACE
                         if (warp == 0 && lane == 0 && gi == 1 && j == 40 && sev_trace_buf)
                             for (int k = 0; k < 6; ++k) sev_trace_buf[3 * 4096 * 8 + 4000 * 8 + k] = sev_trace_phase[k];

@@ -76,16 +76,24 @@ __device__ __forceinline__ void tri_reflector(T x, int nr, T &v, T &tau, T &beta
 // lane t, tau, beta) arrives in registers; if the sweep has a next chase,
 // its reflector -- a function of column o after this chase only -- is formed
 // here and returned the same way (its column gets [beta'; 0]).
-template <typename T, int B>
-__device__ __forceinline__ void tri_chase(int n, int o, int j, bool has_next, const TriWin<T, B> &W, T *vbuf,
+// FULL: an interior chase (j > 1, o + 3b <= n, a next chase follows), where
+// every block has its full size: the sizes are compile-time constants and
+// the per-lane bounds tests on n drop out.
+template <typename T, int B, bool FULL = false>
+__device__ __forceinline__ void tri_chase(int n, int o, int j, bool has_next_rt, const TriWin<T, B> &W, T *vbuf,
                                           T *wbuf, T &v, T &tau, T &beta) {
     constexpr int LDW = 2 * B;
     const int lane = threadIdx.x & 31;
     const int wcap = W.wcap;
     T *const w = W.w;
-    const int n_r = min(n - o, B);
+    const bool has_next = FULL ? true : has_next_rt;
+    const int n_r = FULL ? B : min(n - o, B);
     int up0, nc, ov;
-    if (j == 1) {
+    if (FULL) {
+        up0 = o - B + 1;
+        nc = 3 * B - 1;
+        ov = B - 1;
+    } else if (j == 1) {
         up0 = o;
         nc = min(n - o, 2 * B);
         ov = 0;
@@ -144,7 +152,7 @@ __device__ __forceinline__ void tri_chase(int n, int o, int j, bool has_next, co
     TRACEP(2);
     // the next chase's reflector: column o of the rows below, x_t = rb[0] of lane t
     T nv = T(0), ntau = T(0), nbeta = T(0);
-    const int n_r_next = has_next ? min(n - (o + B), B) : 0;
+    const int n_r_next = FULL ? B : (has_next ? min(n - (o + B), B) : 0);
     if (has_next) tri_reflector<T, B>(rb[0], n_r_next, nv, ntau, nbeta);
     TRACEP(3);
     // qr-row block: H X H = X - v w^T - w v^T, w = p - (tau/2)(p^T v) v
