@@ -143,31 +143,66 @@ __global__ void bisect_prep_kernel(int n, const double *__restrict__ d, const do
     }
 }
 
+// One step of the minors recurrence with t = d_i sc - x: u = e_{i-1}^2 a,
+// p = t b - u; sign, zero test and exponent from the bits (integer work, so
+// the FP64 pipe sees only the three operations), rescaling by a power of two
+// when |p| leaves [2^-256, 2^256].
+__device__ __forceinline__ void sturm_step(double di, double e2i, double x, double sc, double &a, double &b,
+                                           bool &neg, int &c) {
+    const double t = __fma_rn(di, sc, -x);
+    const double u = __dmul_rn(e2i, a);
+    const double p = __fma_rn(t, b, -u);
+    const long long pb = __double_as_longlong(p);
+    const bool zero = (pb << 1) == 0;
+    const bool pn = zero ? !neg : pb < 0;
+    c += pn != neg;
+    neg = pn;
+    a = b;
+    b = p;
+    const int ex = (int)((pb >> 52) & 0x7FF);
+    if (__builtin_expect(ex > 1023 + 256 || (ex < 1023 - 256 && !zero), 0)) {
+        int k = 1023 - ex;
+        k = k > 512 ? 512 : (k < -512 ? -512 : k);
+        const double f = pow2_exact(k);
+        a = __dmul_rn(a, f);
+        b = __dmul_rn(b, f);
+    }
+}
+
+// The loads of d and e^2 do not depend on the recurrence, so blocks of kSturmU
+// steps are loaded one block ahead (the chain waits on the FP64 pipe, not on
+// a memory latency per step); the operations and their order are those of
+// the plain loop.
+constexpr int kSturmU = 4;
 __device__ __forceinline__ int sturm_count(int n, const double *__restrict__ d, const double *__restrict__ e2s,
                                            double x, double sc) {
     double a = 1.0, b = __fma_rn(__ldg(d), sc, -x);
     bool neg = b <= 0.0;  // p_0 = 1 > 0: a zero p_1 counts as negative
     int c = neg;
-    for (int i = 1; i < n; ++i) {
-        const double t = __fma_rn(__ldg(d + i), sc, -x);
-        const double u = __dmul_rn(__ldg(e2s + i - 1), a);
-        const double p = __fma_rn(t, b, -u);
-        // sign, zero test and exponent from the bits: integer work, so the
-        // FP64 pipe sees only the three operations above
-        const long long pb = __double_as_longlong(p);
-        const bool zero = (pb << 1) == 0;
-        const bool pn = zero ? !neg : pb < 0;
-        c += pn != neg;
-        neg = pn;
-        a = b;
-        b = p;
-        const int ex = (int)((pb >> 52) & 0x7FF);
-        if (__builtin_expect(ex > 1023 + 256 || (ex < 1023 - 256 && !zero), 0)) {
-            int k = 1023 - ex;
-            k = k > 512 ? 512 : (k < -512 ? -512 : k);
-            const double f = pow2_exact(k);
-            a = __dmul_rn(a, f);
-            b = __dmul_rn(b, f);
+    double dn[kSturmU], en[kSturmU];
+#pragma unroll
+    for (int u = 0; u < kSturmU; ++u) {
+        const int i = 1 + u;
+        dn[u] = i < n ? __ldg(d + i) : 0.0;
+        en[u] = i < n ? __ldg(e2s + i - 1) : 0.0;
+    }
+    for (int i0 = 1; i0 < n; i0 += kSturmU) {
+        double dc[kSturmU], ec[kSturmU];
+#pragma unroll
+        for (int u = 0; u < kSturmU; ++u) {
+            dc[u] = dn[u];
+            ec[u] = en[u];
+            const int i = i0 + kSturmU + u;
+            dn[u] = i < n ? __ldg(d + i) : 0.0;
+            en[u] = i < n ? __ldg(e2s + i - 1) : 0.0;
+        }
+        if (i0 + kSturmU <= n) {
+#pragma unroll
+            for (int u = 0; u < kSturmU; ++u) sturm_step(dc[u], ec[u], x, sc, a, b, neg, c);
+        } else {
+#pragma unroll
+            for (int u = 0; u < kSturmU; ++u)
+                if (i0 + u < n) sturm_step(dc[u], ec[u], x, sc, a, b, neg, c);
         }
     }
     return c;
