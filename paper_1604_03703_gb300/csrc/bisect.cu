@@ -340,6 +340,9 @@ struct BisWs {
     BisCtl *ctl;
 };
 
+#ifndef SEV_BIS_CHAINS_PER_SM
+#define SEV_BIS_CHAINS_PER_SM 64
+#endif
 constexpr int kBisThreads = 1024;
 constexpr int kBisMaxItems = 131072;
 
@@ -528,7 +531,7 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     // three chains each, ran 18 % slower); 1024 threads per CTA run a round
     // of up to 150K chains in a single pass.
     const int grid = h->sm_count;
-    int budget = grid * 64;
+    int budget = grid * SEV_BIS_CHAINS_PER_SM;
     int maxit = 200;
     void *args[] = {(void *)&n, (void *)&d, (void *)&e2, (void *)&par, (void *)&rtol, (void *)&maxit,
                     (void *)&budget, (void *)&eigs, (void *)&W, (void *)&h->d_err};

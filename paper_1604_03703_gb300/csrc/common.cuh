@@ -868,7 +868,7 @@ __device__ __forceinline__ void batched_copy(int count, int t, int nt, Src src, 
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int k = base + u * nt;
-            v[u] = k < count ? src(k) : T(0);
+            v[u] = k < count ? src(k) : T{};
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {

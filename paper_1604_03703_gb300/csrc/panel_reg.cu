@@ -156,13 +156,23 @@ __global__ void __launch_bounds__(kRegThreads, 1)
     const int rows = nc * b;
     const int nr = nref[node];
     const T *Y = Ylev + (size_t)p * ystride;
-    batched_copy<T>(
-        nr * 32 * R, threadIdx.x, blockDim.x,
-        [&](int idx) {
-            const int k = idx / (32 * R), r = idx % (32 * R);
-            return r < rows ? Y[r + (size_t)k * rows] : T(0);
-        },
-        [&](int idx, T v) { Vs[idx] = v; });
+    if (rows == 32 * R && ((uintptr_t)Y & 15) == 0) {
+        // the node's reflectors fill whole 32R-row columns: one contiguous
+        // block, copied in 16-byte pieces, 8 in flight per thread
+        const uint4 *src = reinterpret_cast<const uint4 *>(Y);
+        uint4 *dst = reinterpret_cast<uint4 *>(Vs);
+        batched_copy<uint4, 8>(
+            (int)(((size_t)nr * rows * sizeof(T)) / 16), threadIdx.x, blockDim.x, [&](int i) { return __ldg(src + i); },
+            [&](int i, uint4 v) { dst[i] = v; });
+    } else {
+        batched_copy<T>(
+            nr * 32 * R, threadIdx.x, blockDim.x,
+            [&](int idx) {
+                const int k = idx / (32 * R), r = idx % (32 * R);
+                return r < rows ? Y[r + (size_t)k * rows] : T(0);
+            },
+            [&](int idx, T v) { Vs[idx] = v; });
+    }
     for (int k = threadIdx.x; k < nr; k += blockDim.x) taus[k] = tau[(size_t)node * b + k];
     const T *Zn = Zbuf + (size_t)node * b * b;
     T m[Q][R], cm[Q];

@@ -369,21 +369,26 @@ __global__ void __launch_bounds__(256) utx_partial_kernel(int N, int b, int chun
         }
 }
 
-// Zm = T^T (sum_s P_s): CTA handles 16 columns; sums the partials in a fixed
-// order (deterministic), then applies T^T.
+// M = sum_s P_s, entry by entry, the partials in a fixed order (deterministic).
 template <typename T>
-__global__ void __launch_bounds__(256) utx_reduce_kernel(int b, int nparts, const T *__restrict__ part,
-                                                         const T *__restrict__ Tm, T *__restrict__ Zm) {
+__global__ void __launch_bounds__(256) utx_sum_kernel(int bb, int nparts, const T *__restrict__ part, T *__restrict__ M) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= bb) return;
+    T s = 0;
+    for (int p = 0; p < nparts; ++p) s += part[(size_t)p * bb + idx];
+    M[idx] = s;
+}
+
+// Zm = T^T M (M = sum_s P_s, b x b; T upper triangular): CTA handles 4
+// columns; Zm(a, c) = sum_{q <= a} T(q, a) M(q, c), summed in q order.
+template <typename T>
+__global__ void __launch_bounds__(256) utx_tmul_kernel(int b, const T *__restrict__ M, const T *__restrict__ Tm,
+                                                       T *__restrict__ Zm) {
     extern __shared__ __align__(16) unsigned char smem[];
-    T *Ms = (T *)smem;  // b x 16
-    const int c0 = blockIdx.x * 16;
-    const int nc = min(16, b - c0);
-    for (int idx = threadIdx.x; idx < b * nc; idx += blockDim.x) {
-        const int a = idx % b, c = idx / b;
-        T s = 0;
-        for (int p = 0; p < nparts; ++p) s += part[(size_t)p * b * b + a + (size_t)(c0 + c) * b];
-        Ms[a + (size_t)c * b] = s;
-    }
+    T *Ms = (T *)smem;  // b x 4
+    const int c0 = blockIdx.x * 4;
+    const int nc = min(4, b - c0);
+    for (int idx = threadIdx.x; idx < b * nc; idx += blockDim.x) Ms[idx] = M[idx % b + (size_t)(c0 + idx / b) * b];
     __syncthreads();
     for (int idx = threadIdx.x; idx < b * nc; idx += blockDim.x) {
         const int a = idx % b, c = idx / b;
@@ -444,8 +449,10 @@ struct F2BBuffers {
 
 constexpr int kSymmMaxSplits = 8;
 
+// Row chunks of U^T X: 256 rows or more each, at most 64 (a wave of CTAs at
+// b = 128: 2 x 2 tiles x 64 chunks).
 static int utx_parts(int N) {
-    int p = (N + 1023) / 1024;
+    int p = (N + 255) / 256;
     return p < 1 ? 1 : (p > 64 ? 64 : p);
 }
 
@@ -457,7 +464,7 @@ static void carve_f2b(Carver &c, F2BBuffers<T> &B, sev_ctx *h, int n, int b, boo
     B.V = c.take<T>((size_t)n * b);
     B.Tm = c.take<T>((size_t)b * b);
     B.Zm = c.take<T>((size_t)b * b);
-    B.part = c.take<T>((size_t)utx_parts(n) * b * b);
+    B.part = c.take<T>((size_t)(utx_parts(n) + 1) * b * b);  // the chunks' partial products, then their sum
     B.ypart = c.take<T>((size_t)kSymmMaxSplits * n * b);
     B.tc_ws = tc ? (void *)c.take<char>(tc_workspace<T>(n, b)) : nullptr;
     B.panel_ws = c.take<char>(panel_workspace<T>(h, n, b));
@@ -519,8 +526,13 @@ int launch_full_to_band(sev_ctx *h, int n, T *A, int lda, int b, T *AB, int ldab
         const int chunk = (((N + parts - 1) / parts) + BK - 1) / BK * BK;
         SEV_LAUNCH(h, K_VFORM_UTX, utx_partial_kernel<T>, dim3((b + BM - 1) / BM, (b + BN - 1) / BN, parts), 256, 0, N,
                    b, chunk, B.U, N, B.X, N, B.part);
-        SEV_LAUNCH(h, K_VFORM_REDUCE, utx_reduce_kernel<T>, (b + 15) / 16, 256, sizeof(T) * (size_t)b * 16, b, parts,
-                   B.part, B.Tm, B.Zm);
+        {
+            // the chunks summed by b^2 threads, then T^T applied (4 columns a CTA)
+            T *Msum = B.part + (size_t)parts * b * b;
+            SEV_LAUNCH(h, K_VFORM_REDUCE, utx_sum_kernel<T>, (b * b + 255) / 256, 256, 0, b * b, parts, B.part, Msum);
+            SEV_LAUNCH(h, K_VFORM_REDUCE, utx_tmul_kernel<T>, (b + 3) / 4, 256, sizeof(T) * (size_t)b * 4, b, Msum,
+                       B.Tm, B.Zm);
+        }
         // V = 1/2 U Zm - X
         SEV_LAUNCH(h, K_VFORM_V, gemm_nn_kernel<T>, dim3((N + BM - 1) / BM, (b + BN - 1) / BN), 256, 0, N, b, b,
                    T(0.5), B.U, N, B.Zm, b, T(-1), B.X, N, B.V, N);
