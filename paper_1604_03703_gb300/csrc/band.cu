@@ -150,8 +150,12 @@ size_t band_smem_bytes(int b, int h) {
 // The qr-row diagonal block X_d (n_r x n_r, mirrored in S.Xs) after U, T
 // and U T are formed: W_d = X_d (U T); S = U^T W_d; Z = T^T S; V_d = -W_d +
 // U Z / 2; X_d += U V_d^T + V_d U^T; the lower triangle written back.
+#ifndef SEV_CHASE_PART_INLINE
+#define SEV_CHASE_PART_INLINE
+#endif
 template <typename T>
-__device__ void chase_diag_update(T *AB, int ldab, int n, int n_r, int nr, int o_qr_r, ChaseSmem<T> &S, int &bad) {
+__device__ SEV_CHASE_PART_INLINE void chase_diag_update(T *AB, int ldab, int n, int n_r, int nr, int o_qr_r,
+                                                        ChaseSmem<T> &S, int &bad) {
     const int ldb1 = S.ldb1, ldh1 = S.ldh1;
     const int tid = threadIdx.x, nt = blockDim.x;
     constexpr bool kVec = sizeof(T) == 4;
@@ -457,8 +461,8 @@ __device__ __forceinline__ P *cluster_map(P *p, unsigned rank) {
 // the block <-> band position (row0 + a) for rank 2 or column (col0 + a) for
 // rank 1): W = X (U T); X <- X - W U^T; written back.
 template <typename T>
-__device__ void chase_rows_update(T *AB, int ldab, int n, int rows, int n_r, int nr, int o_qr_r, int base, bool above,
-                                  ChaseSmem<T> &S, int &bad) {
+__device__ SEV_CHASE_PART_INLINE void chase_rows_update(T *AB, int ldab, int n, int rows, int n_r, int nr, int o_qr_r,
+                                                        int base, bool above, ChaseSmem<T> &S, int &bad) {
     const int ldb1 = S.ldb1, tid = threadIdx.x, nt = blockDim.x;
     constexpr bool kVec = sizeof(T) == 4;
     T *X = S.Xs;

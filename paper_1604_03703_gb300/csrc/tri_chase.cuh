@@ -79,8 +79,15 @@ __device__ __forceinline__ void tri_reflector(T x, int nr, T &v, T &tau, T &beta
 // FULL: an interior chase (j > 1, o + 3b <= n, a next chase follows), where
 // every block has its full size: the sizes are compile-time constants and
 // the per-lane bounds tests on n drop out.
+// A chase is compiled as a function of its own: inlined into the
+// sliding-window kernel, whose loader and writer code shares the register
+// allocation, its stores alone took ~2.8K cycles against ~0.5K (16 -> 1
+// stage 222 -> 180 ms at n = 16384).
+#ifndef SEV_TRI_CHASE_INLINE
+#define SEV_TRI_CHASE_INLINE __noinline__
+#endif
 template <typename T, int B, bool FULL = false>
-__device__ __forceinline__ void tri_chase(int n, int o, int j, bool has_next_rt, const TriWin<T, B> &W, T *vbuf,
+__device__ SEV_TRI_CHASE_INLINE void tri_chase(int n, int o, int j, bool has_next_rt, const TriWin<T, B> &W, T *vbuf,
                                           T *wbuf, T &v, T &tau, T &beta) {
     constexpr int LDW = 2 * B;
     const int lane = threadIdx.x & 31;
