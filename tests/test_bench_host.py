@@ -30,6 +30,28 @@ def test_band_models_follow_the_schedule():
     assert chase == pytest.approx(2 * 4 * (4 + 2) * n ** 2)
 
 
+def test_band_models_follow_a_tuned_schedule():
+    """With the schedule the autotuner chose (128 -> 32 -> 8 -> 1), the band
+    work models follow it: 128 -> 32 (k = 4) and 32 -> 8 (k = 4) are chases,
+    8 -> 1 is the sliding-window stage."""
+    n = 16384
+    sched = [128, 32, 8, 1]
+    chase, _, _ = bench.kernel_model("band_chase", n, 128, 4, sched)
+    assert chase == pytest.approx(2 * 4 * (4 + 4) * n ** 2)
+    tri, _, _ = bench.kernel_model("band_tri", n, 128, 4, sched)
+    assert tri == pytest.approx(2 * 4 * 8 * n ** 2)
+
+
+def test_measured_traffic_is_tied_to_its_schedule():
+    """The DRAM bytes recorded for a kernel belong to the schedule they were
+    taken on; the bench drops them for any other schedule."""
+    for name, t in bench.MEASURED_TRAFFIC.items():
+        assert t["bytes_per_step"] > 0 and t["note"]
+        assert t["schedule"][0] == 128 and t["schedule"][-1] == 1
+        b = t["schedule"]
+        assert all(x % y == 0 for x, y in zip(b[:-1], b[1:]))
+
+
 def test_roofline_arithmetic():
     peaks = {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1500.0}
     r = bench.roofline("band_chase", 3.0e9, "byte", "hbm", 1000.0, peaks, {"sm_mhz": 2000.0}, 4)
