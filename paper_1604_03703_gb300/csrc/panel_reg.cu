@@ -2,25 +2,27 @@
 // QR step of Algorithm 4.1: tree QR of Algorithm 3.2, then Householder
 // reconstruction of Cor. 3.7) with the matrix blocks held in REGISTERS.
 //
-// Register tile.  A CTA of 16 warps holds a (32 R) x (16 Q) block: lane l of
-// warp w keeps a[q][t] = M(l + 32 t, w + 16 q).  Columns are dealt to the
+// Register tile.  A CTA of NW warps holds a (32 R) x (NW Q) block: lane l
+// of warp w keeps a[q][t] = M(l + 32 t, w + NW q).  Columns are dealt to the
 // warps cyclically, so the active (not yet factorised) columns stay spread
 // over all warps as the factorisation proceeds, and every row of a column
 // sits in one warp, so a column's dot product is a lane-local sum followed
-// by one warp butterfly.
+// by one warp butterfly.  The leaf and node QRs of FP32 panels run on 8
+// warps (fewer warps share each scheduler with the column owner), the
+// applies and the reconstruction on 16.
 //
-// QR (reg_qr).  Householder QR, one reflector per column, one __syncthreads
-// per column.  At step k every warp applies H_k = I - tau_k v_k v_k^T to its
-// columns c > k; the warp owning column k+1 does that column first and
-// forms reflector k+1 from it (lookahead) before its other columns, so the
-// serial chain per column is one apply plus one norm.  v_k travels through a
-// double-buffered shared vector.  Scalars: the "always reflect" rule,
-// beta = -sgn(alpha) ||x||, tau = (beta - alpha)/beta (FP64-accurate for FP32
-// data through the pair-float routine, see common.cuh).  Stacked triangles
-// (the tree nodes) are handled with their structure: reflector k is nonzero
-// only in row k of the top triangle and rows 0..k of the lower ones (the
-// other entries are exact zeros), so 32-row blocks without such a row are
-// skipped -- bit for bit the same result as the dense loop.
+// QR (reg_qr, regtile.cuh).  Householder QR, one reflector per column, one
+// barrier per column.  At step k the warp owning column k+1 applies H_k to
+// that column and forms reflector k+1 from it (lookahead), leaving its other
+// columns to the next step; every other warp applies H_k = I - tau_k v_k
+// v_k^T to its columns c > k.  v_k travels through three shared buffers.
+// Scalars: the "always reflect" rule, beta = -sgn(alpha) ||x||,
+// tau = (beta - alpha)/beta (FP64-accurate for FP32 data through the
+// pair-float routine, see common.cuh).  Stacked triangles (the tree nodes)
+// are handled with their structure: reflector k is nonzero only in row k of
+// the top triangle and rows 0..k of the lower ones (the other entries are
+// exact zeros), so 32-row blocks without such a row are skipped -- bit for
+// bit the same result as the dense loop.
 //
 // Apply (reg_apply_all).  M <- H_0 H_1 ... H_{r-1} M with all reflectors in
 // shared memory and M's columns private to their warps: no barrier at all.
