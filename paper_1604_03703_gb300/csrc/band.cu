@@ -24,6 +24,11 @@
 // its sweep before taking another, so every awaited sweep is held by a
 // running CTA: the waits cannot deadlock.  Every wait is capped; on expiry
 // the kernel latches SEV_ERR_TIMEOUT and returns.
+//
+// Bands of width 64 or more run each sweep on a cluster of three CTAs
+// (band_chase_x3_kernel, below): the QR and the diagonal block on one CTA,
+// the rows above and below on the other two, with the same arithmetic per
+// entry as the one-CTA chase.
 #include "regtile.cuh"
 
 #ifdef SEV_TRACE
