@@ -95,12 +95,14 @@ int sev_set_workspace(sev_handle handle, void *workspace, size_t bytes);
 /*
  * Eigenvalues of the symmetric n x n matrix A (Algorithm 4.3):
  * full-to-band to half-bandwidth b0, band-to-band stages down to the
- * tridiagonal with the widths sev_band_schedule reports (e.g. 128 -> 32 ->
- * 16 -> 1, 64 -> 16 -> 1, 16 -> 1), bisection.
+ * tridiagonal, bisection.  The stage widths are the ones sev_eigvalsh_bands
+ * reports: those sev_autotune chose on this handle for the bucket of n and
+ * prec, else the fixed rule of sev_band_schedule (e.g. 128 -> 32 -> 16 -> 1).
  *   A      device, n x n, leading dimension lda >= max(1, n); double for
  *          SEV_FP64, float for SEV_MIXED; lower triangle read, overwritten.
  *   b0     first half-bandwidth, 1 <= b0 (values >= n-1 skip full-to-band);
- *          0 picks the library's default for (n, prec).
+ *          0 picks the tuned b0 for (n, prec) if sev_autotune set one, else
+ *          the library's default.
  *   eigs   device, n doubles, ascending on completion.
  * Bisection tolerance: relative 1e-14 (SEV_FP64) or 1e-9 (SEV_MIXED) of the
  * Gershgorin bound of the tridiagonal.
