@@ -184,9 +184,9 @@ __device__ bool batch_band_to_tri(const T *A, int n, int lda, unsigned char *sme
                 __syncwarp();
             }
             if (j > 1 && j < Ji && o + 3 * B <= n)
-                tri_chase<T, B, true>(n, o, j, true, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
+                tri_chase_body<T, B, true>(n, o, j, true, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
             else
-                tri_chase<T, B>(n, o, j, j < Ji, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
+                tri_chase_body<T, B>(n, o, j, j < Ji, W, vb + warp * 32, wb + warp * 32, rv, rtau, rbeta);
             __threadfence_block();
             __syncwarp();
             if (lane == 0) sval[(i - 1) % kBatchWarps] = i * 2048 + (j == Ji ? kDone : j);

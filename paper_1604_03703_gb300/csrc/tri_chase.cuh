@@ -87,8 +87,8 @@ __device__ __forceinline__ void tri_reflector(T x, int nr, T &v, T &tau, T &beta
 #define SEV_TRI_CHASE_INLINE __noinline__
 #endif
 template <typename T, int B, bool FULL = false>
-__device__ SEV_TRI_CHASE_INLINE void tri_chase(int n, int o, int j, bool has_next_rt, const TriWin<T, B> &W, T *vbuf,
-                                          T *wbuf, T &v, T &tau, T &beta) {
+__device__ __forceinline__ void tri_chase_body(int n, int o, int j, bool has_next_rt, const TriWin<T, B> &W,
+                                               T *vbuf, T *wbuf, T &v, T &tau, T &beta) {
     constexpr int LDW = 2 * B;
     const int lane = threadIdx.x & 31;
     const int wcap = W.wcap;
@@ -192,6 +192,14 @@ __device__ SEV_TRI_CHASE_INLINE void tri_chase(int n, int o, int j, bool has_nex
     v = nv;
     tau = ntau;
     beta = nbeta;
+}
+
+// The chase as the sliding-window kernel calls it (see SEV_TRI_CHASE_INLINE);
+// the batched kernel inlines tri_chase_body, which is faster there.
+template <typename T, int B, bool FULL = false>
+__device__ SEV_TRI_CHASE_INLINE void tri_chase(int n, int o, int j, bool has_next_rt, const TriWin<T, B> &W, T *vbuf,
+                                               T *wbuf, T &v, T &tau, T &beta) {
+    tri_chase_body<T, B, FULL>(n, o, j, has_next_rt, W, vbuf, wbuf, v, tau, beta);
 }
 
 }  // namespace sev
